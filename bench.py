@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark: staggered even-odd CG (Dslash inside CG) on one GB300, through the C-ABI.
+
+One step = one pass of the whole hot path on one synthetic problem: pack the gauge field
+(qcd_load_links), run the even-odd CG to a relative true residual of 1e-10 with the fused
+Dslash/CG kernels, form y = D_oe x and recompute the FP64 true residual (qcd_cg_solve).
+
+value = Dslash GFLOP/s sustained inside the solve: 570 flop per output site of every
+half-lattice operator application the solve performs (2 per CG iteration, 2 more for y and
+the true residual, 2 per reliable update), divided by the step's device time.
+
+Timing: W untimed warm-up steps, then exactly K timed steps, each bracketed by CUDA events on
+the library's stream; the L2 cache is flushed (a 512 MB write) before every step, outside the
+events. Under torchrun each rank runs an independent replica (the solve does not shard).
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GFLOP/s & %HBM roofline; CG time-to-1e-10, mixed/batched vs FP64"
+FLOP_PER_SITE = 570
+# FP64 FMA peak of GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    # the 16^4 FP64 workload: Haar links, m = 0.1, plain FP64 even-odd CG
+    "cg16_fp64": dict(dims=(16, 16, 16, 16), kind="haar", mass=0.1, tol=1e-10, inner="double",
+                      desc="staggered 16^4 Haar SU(3), m=0.1, plain FP64 even-odd CG to true rel. residual 1e-10"),
+    "cg16_fp64_nearid_m0.02": dict(dims=(16, 16, 16, 16), kind="near_identity", mass=0.02, tol=1e-10, inner="double",
+                                   desc="staggered 16^4 near-identity (eps=0.3), m=0.02, FP64 CG to 1e-10"),
+    "cg32_fp64": dict(dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="double",
+                      desc="staggered 32^4 Haar SU(3), m=0.01, plain FP64 even-odd CG to 1e-10"),
+    "cg32_single12": dict(dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="single12",
+                          desc="staggered 32^4 Haar, m=0.01, mixed CG: FP32 recon-12 inner, FP64 reliable updates"),
+    "cg32_half12": dict(dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="half12",
+                        desc="staggered 32^4 Haar, m=0.01, mixed CG: FP16+scale recon-12 inner, FP64 reliable updates"),
+}
+DEFAULT_WORKLOAD = "cg16_fp64"
+PRECS = {"double": (0, 18), "single18": (1, 18), "single12": (1, 12), "half12": (2, 12)}
+DTYPE = {"double": "f64", "single18": "f32 (FP64 reliable updates)", "single12": "f32 (FP64 reliable updates)",
+         "half12": "f16-storage/f32 (FP64 reliable updates)"}
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _clock_sampler(device_uuid):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"]
+    if device_uuid:
+        cmd += ["-i", device_uuid]
+    try:
+        p = subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL)
+    except (OSError, ValueError):
+        return None, f.name
+    return p, f.name
+
+
+def _clock_summary(proc, path):
+    if proc is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    sm, smax, power, reasons = [], [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    with open(path) as fh:
+        for line in fh:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _half_dslash_count(info):
+    return 2 * info["iterations"] + 2 + 2 * info["reliable_updates"]
+
+
+def run_gpu(args, wl):
+    import numpy as np
+    import torch
+
+    from paper_1311_2719_gb300 import inputs as I
+    from paper_1311_2719_gb300 import qcd as Q
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dims, mass, tol, inner = wl["dims"], wl["mass"], wl["tol"], wl["inner"]
+    U = I.make_links(dims, kind=wl["kind"], seed=1)
+    b = I.make_source(dims, seed=2)
+    V = U.shape[0]
+    Vh = V // 2
+
+    stream = torch.cuda.Stream()
+    lat = Q.Lattice(dims)
+    U_host = torch.from_numpy(U).pin_memory()
+    b_host = torch.from_numpy(b).pin_memory()
+    U_dev = U_host.to("cuda", non_blocking=False)
+    b_dev = b_host.to("cuda", non_blocking=False)
+    x_dev = torch.zeros_like(b_dev)
+    y_dev = torch.zeros_like(b_dev)
+    x_host = torch.empty_like(b_host).pin_memory()
+    y_host = torch.empty_like(b_host).pin_memory()
+    packed = {}
+    prec_in, recon_in = PRECS[inner]
+    for p, r in {(0, 18), (prec_in, recon_in)}:
+        packed[p] = (lat.empty_bytes(Q.qcd_links_bytes(lat.handle, p, r)), r)
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner, opts.recon_inner = prec_in, recon_in
+    opts.profile = 1
+    ws = lat.workspace(opts)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step(host_io=False):
+        launches = 0
+        with torch.cuda.stream(stream):
+            if host_io:
+                U_dev.copy_(U_host, non_blocking=True)
+                b_dev.copy_(b_host, non_blocking=True)
+            for p, (buf, r) in packed.items():
+                Q.qcd_load_links(lat.handle, U_dev, buf, p, r, stream)
+                launches += 1
+            rc, info = Q.qcd_cg_solve(lat.handle, x_dev, b_dev, mass, tol, 100000, opts, ws, y_dev, stream=stream)
+            if host_io:
+                x_host.copy_(x_dev, non_blocking=True)
+                y_host.copy_(y_dev, non_blocking=True)
+        if rc != Q.QCD_OK:
+            raise RuntimeError(f"solve failed: {Q.qcd_status_string(rc)} {info}")
+        info["launches"] = launches + info["kernel_launches"]
+        return info
+
+    def timed(n, host_io=False):
+        ms, infos = [], []
+        for _ in range(n):
+            flush.fill_(1)  # evict L2 between steps (outside the timed events)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step(host_io))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    proc, cpath = _clock_sampler(uuid)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    ms, infos = timed(args.steps)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clocks = _clock_summary(proc, cpath)
+    if world > 1:
+        dist.barrier()
+    ms_e2e, infos_e2e = timed(args.steps, host_io=True)
+    torch.cuda.synchronize()
+    # the same solve replayed as CUDA graphs without per-launch events (reported beside)
+    opts.profile = 0
+    ms_graph, _ = timed(args.steps)
+    opts.profile = 1
+
+    flops = [FLOP_PER_SITE * Vh * _half_dslash_count(i) for i in infos]
+    total_ms = sum(ms)
+    total_ms_e2e = sum(ms_e2e)
+    flops_e2e = [FLOP_PER_SITE * Vh * _half_dslash_count(i) for i in infos_e2e]
+    tot = torch.tensor([total_ms, total_ms_e2e], dtype=torch.float64, device="cuda")
+    fl = torch.tensor([sum(flops), sum(flops_e2e)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        dist.all_reduce(fl, op=dist.ReduceOp.SUM)
+    total_ms, total_ms_e2e = tot.tolist()
+    sum_flops, sum_flops_e2e = fl.tolist()
+    value = sum_flops / (total_ms * 1e-3) / 1e9
+    e2e_value = sum_flops_e2e / (total_ms_e2e * 1e-3) / 1e9
+
+    # dominant kernel: the half-lattice operator launches inside the iterations (CUDA events)
+    d_ms = sum(i["dslash_ms"] for i in infos)
+    d_n = sum(i["dslash_launches"] for i in infos)
+    per_launch_ms = d_ms / d_n
+    achieved_tflops = FLOP_PER_SITE * Vh / (per_launch_ms * 1e-3) / 1e12
+    if inner == "double":
+        link_b, vec_b = 1152, 96
+    elif inner == "single18":
+        link_b, vec_b = 576, 48
+    elif inner == "single12":
+        link_b, vec_b = 384, 48
+    else:
+        link_b, vec_b = 192, 32
+    alg_bytes = (link_b + vec_b) * Vh
+    achieved_gbs = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if inner == "double":
+        roofline = {"bound": "alu", "kernel": "dslash_kernel (CG K1+K2 launches)", "achieved": round(achieved_tflops, 4),
+                    "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
+                    "peak_source": "derived FP64 FMA peak (152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz)",
+                    "traffic": None,
+                    "hbm_model_gbs": round(achieved_gbs, 1), "hbm_model_frac": round(achieved_gbs / hbm_peak, 4),
+                    "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": FLOP_PER_SITE * Vh,
+                    "avg_launch_us": round(per_launch_ms * 1e3, 3)}
+    else:
+        roofline = {"bound": "hbm", "kernel": "dslash_kernel (CG K1+K2 launches)", "achieved": round(achieved_gbs, 1),
+                    "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 4),
+                    "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
+                    "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": FLOP_PER_SITE * Vh,
+                    "achieved_tflops": round(achieved_tflops, 4), "avg_launch_us": round(per_launch_ms * 1e3, 3)}
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[inner], "data": "synthetic (seeded Haar/near-identity SU(3) links, Gaussian source)",
+        "config": {"workload": wl["desc"], "dims": list(dims), "mass": mass, "tol": tol, "inner": inner,
+                   "parallelism": f"replicas x{world} (no sharding)",
+                   "l2": "flushed before every step (512 MB write, outside the timed events)",
+                   "step": "qcd_load_links + qcd_cg_solve (CG, y = D_oe x, FP64 true residual)"},
+        "cg": {"iterations": infos[-1]["iterations"], "true_rel_residual": infos[-1]["true_rel_residual"],
+               "reliable_updates": infos[-1]["reliable_updates"], "time_to_solution_ms": round(total_ms / args.steps, 4),
+               "half_dslash_per_solve": _half_dslash_count(infos[-1])},
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int(U_host.numel() * 16 + b_host.numel() * 16),
+                "d2h_bytes_per_step": int(x_host.numel() * 16 + y_host.numel() * 16),
+                "ms_per_step": round(total_ms_e2e / args.steps, 4)},
+        "gpu_launches": int(sum(i["launches"] for i in infos)),
+        "clocks": clocks,
+        "wall_s_timed_region": round(t_wall, 4),
+        "ms_per_step_graph_unprofiled": round(sum(ms_graph) / args.steps, 4),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_iters)
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def _oracle_sample(wl, iters, U=None, b=None):
+    """Time the FP64 oracle CG, as it stands, for `iters` iterations of the workload."""
+    from oracle import staggered as S
+    from paper_1311_2719_gb300 import inputs as I
+
+    dims = wl["dims"]
+    if U is None:
+        U = I.make_links(dims, kind=wl["kind"], seed=1)
+        b = I.make_source(dims, seed=2)
+    t0 = time.perf_counter()
+    res = S.cg_solve(U, b, dims, wl["mass"], wl["tol"], iters)
+    dt = time.perf_counter() - t0
+    Vh = U.shape[0] // 2
+    flops = FLOP_PER_SITE * Vh * (2 * res["iterations"] + 2)
+    return flops, dt, res["iterations"]
+
+
+def cpu_baseline(wl, iters):
+    flops, dt, n = _oracle_sample(wl, iters)
+    return {"value": round(flops / dt / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle CG on the same {wl['dims']} workload, first {n} iterations + y + true "
+                      f"residual ({dt:.1f} s), algorithmic 570 flop/site per half-lattice operator"}
+
+
+def run_reference(args, wl):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return None
+    from paper_1311_2719_gb300 import inputs as I
+
+    dims = wl["dims"]
+    U = I.make_links(dims, kind=wl["kind"], seed=1)
+    b = I.make_source(dims, seed=2)
+    for _ in range(args.warmup):
+        _oracle_sample(wl, 1, U, b)
+    tot_f, tot_t = 0.0, 0.0
+    n = 0
+    for _ in range(args.steps):
+        f, t, n = _oracle_sample(wl, args.ref_iters, U, b)
+        tot_f += f
+        tot_t += t
+    v = tot_f / tot_t / 1e9
+    sample = (f"each step: FP64 numpy oracle CG on the {dims} workload for {n} iterations + y + true residual "
+              f"(bounded sample), 1 thread")
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Haar SU(3) links, Gaussian source)",
+            "config": {"workload": wl["desc"], "dims": list(dims), "mass": wl["mass"], "tol": wl["tol"],
+                       "parallelism": "cpu oracle, rank 0 only"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-iters", type=int, default=64, help="oracle CG iterations timed for cpu_baseline")
+    ap.add_argument("--ref-iters", type=int, default=12, help="oracle CG iterations per --impl reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    wl = WORKLOADS[args.workload]
+    out = run_reference(args, wl) if args.impl == "reference" else run_gpu(args, wl)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

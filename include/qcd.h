@@ -1,0 +1,185 @@
+/*
+ * qcd.h — C ABI of the GB300 (sm_103a) staggered-fermion Dslash / even-odd CG library.
+ *
+ * The library computes the staggered hopping operator of the paper's matrix-vector
+ * routine (§3) and the conjugate-gradient solve of its congrad routine (§4) on one GPU.
+ *
+ * Operator (the paper does not write it out; this is the convention the library fixes):
+ *   D x(n) = 1/2 sum_mu [ eta_mu(n) zeta_mu(n) U_mu(n) x(n+mu)
+ *                         - eta_mu(n-mu) zeta_mu(n-mu) U_mu(n-mu)^dagger x(n-mu) ]
+ *   eta_mu(n) = (-1)^(x0+...+x_{mu-1}); zeta_3(n) = tbc (default -1) on links with
+ *   x3 = L3-1, else +1. D is anti-Hermitian; M = m + D; M^dagger M = m^2 - D^2.
+ *   Even-odd: parity(n) = (x0+x1+x2+x3) mod 2; D_eo: odd -> even, D_oe: even -> odd;
+ *   the solved operator is A = m^2 - D_eo D_oe on the even sites (Hermitian, >= m^2).
+ *
+ * Layouts
+ *   canonical site index  i = x0 + L0*(x1 + L1*(x2 + L2*x3))   (x0 fastest, x3 = t slowest)
+ *   canonical links       complex128[V][4][3][3]  (links[i][mu] = U_mu(n_i), row-major)
+ *   canonical field       complex128[V][3]
+ *   packed field          the library's even-odd structure-of-arrays layout of ONE parity
+ *                         (V/2 sites) at one precision; size from qcd_field_bytes().
+ *                         Site k of parity p is the canonical site i with i >> 1 == k.
+ *                         QCD_PREC_DOUBLE: double2[3][V/2]; QCD_PREC_SINGLE: float2[3][V/2];
+ *                         QCD_PREC_HALF: 16 bytes per site {3 x half2 colour, float scale}.
+ *   A multi-RHS packed field is nrhs packed fields back to back.
+ *
+ * Memory ownership
+ *   The library never allocates device memory. The caller allocates every device buffer
+ *   (packed links, fields, workspace) and keeps it alive while a handle refers to it.
+ *   Device pointers must be 256-byte aligned. Host pointers are only read during a call.
+ *   All calls that take a stream are asynchronous on that stream unless stated otherwise;
+ *   `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *
+ * Errors
+ *   Every call returns a qcd_status. QCD_ERR_INVALID_ARG leaves all buffers untouched.
+ *   qcd_last_error() gives a thread-local message about the last failing call.
+ */
+#ifndef QCD_H
+#define QCD_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define QCD_API __attribute__((visibility("default")))
+#else
+#define QCD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QCD_OK = 0,
+  QCD_ERR_INVALID_ARG = 1,   /* bad size, pointer, precision, parity, mass or tolerance   */
+  QCD_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in qcd_last_error)    */
+  QCD_ERR_NOT_CONVERGED = 3, /* max_iter reached before the requested tolerance           */
+  QCD_ERR_BREAKDOWN = 4,     /* non-finite or non-positive CG scalar (e.g. NaN in b)      */
+  QCD_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                        */
+  QCD_ERR_UNSUPPORTED = 6,   /* valid request this build does not implement               */
+  QCD_ERR_NO_LINKS = 7       /* qcd_load_links was not called for this precision          */
+} qcd_status;
+
+enum { QCD_EVEN = 0, QCD_ODD = 1 };
+enum { QCD_PREC_DOUBLE = 0, QCD_PREC_SINGLE = 1, QCD_PREC_HALF = 2 };
+enum { QCD_RECON_18 = 18, QCD_RECON_12 = 12 };
+
+typedef struct qcd_lattice qcd_lattice; /* opaque host-side handle */
+
+/* Solver options (qcd_solver_opts_default fills the defaults noted here). */
+typedef struct {
+  int prec_inner;        /* QCD_PREC_DOUBLE (plain FP64 CG, default), _SINGLE or _HALF (mixed) */
+  int recon_inner;       /* link compression for the inner operator: 18 (default) or 12          */
+  double reliable_delta; /* mixed CG: reliable update when |r| < delta * max|r| since the last (0.1) */
+  int reliable_interval; /* mixed CG: and at least every this many iterations (100)              */
+  int check_interval;    /* host reads the device-side convergence flag every k iterations (8)    */
+  int use_graph;         /* replay each k-iteration chunk as a CUDA graph (1)                     */
+  int profile;           /* record CUDA events around every operator launch of the iteration (0);
+                            profiled chunks run as direct launches, not graph replays         */
+} qcd_solver_opts;
+
+/* What a solve reports. */
+typedef struct {
+  int iterations;           /* CG iterations executed                                             */
+  int reliable_updates;     /* FP64 true-residual recomputations inside the solve (mixed CG)      */
+  int converged;            /* 1 when the true residual met tol                                   */
+  int status;               /* the qcd_status the call returned                                   */
+  double true_rel_residual; /* |b_e - A x_e| / |b_e| recomputed in FP64 after the solve           */
+  double iterated_rel_residual; /* sqrt(<r,r>/<b,b>) of the solver's recursion                    */
+  double seconds;           /* wall time of the call (host clock, includes the final sync)        */
+  int kernel_launches;      /* kernels this call launched (graph replays count every node)        */
+  int dslash_launches;      /* operator launches inside the iterations (2 per iteration run)     */
+  double dslash_ms;         /* with opts.profile: summed CUDA-event time of those launches       */
+} qcd_solve_info;
+
+/* ---- status ---------------------------------------------------------------------------------- */
+
+QCD_API const char* qcd_status_string(int status);
+/* Thread-local text about the most recent failing call on this thread ("" if none). */
+QCD_API const char* qcd_last_error(void);
+/* Library version string. */
+QCD_API const char* qcd_version(void);
+
+/* ---- lattice handle -------------------------------------------------------------------------- */
+
+/* Create a handle for an L0 x L1 x L2 x L3 lattice (x3 = t). Every extent must be even and >= 2,
+ * and the volume must be < 2^31. Antiperiodic in t by default. Allocates host memory only. */
+QCD_API int qcd_lattice_create(int L0, int L1, int L2, int L3, qcd_lattice** out);
+QCD_API int qcd_lattice_destroy(qcd_lattice* lat);
+/* Boundary sign zeta on the t-links of the last time slice: +1 (periodic) or -1 (antiperiodic).
+ * Links loaded before the change must be loaded again. */
+QCD_API int qcd_lattice_set_tbc(qcd_lattice* lat, int sign);
+/* Device on which the handle was created (the current device at qcd_lattice_create). */
+QCD_API int qcd_lattice_device(const qcd_lattice* lat);
+
+/* ---- sizes ------------------------------------------------------------------------------------ */
+
+/* Bytes of one packed single-parity field at `prec` (0 on a bad argument). */
+QCD_API size_t qcd_field_bytes(const qcd_lattice* lat, int prec);
+/* Bytes of the packed gauge field at (prec, recon). Supported: DOUBLE/18, SINGLE/18, SINGLE/12,
+ * HALF/12. 0 on an unsupported pair. */
+QCD_API size_t qcd_links_bytes(const qcd_lattice* lat, int prec, int recon);
+/* Bytes of the device workspace qcd_cg_solve needs for these options (nrhs = 1). */
+QCD_API size_t qcd_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts, int nrhs);
+
+QCD_API void qcd_solver_opts_default(qcd_solver_opts* opts);
+
+/* ---- links (paper §4: linkc_acc prepares the device copy of the gauge field) ---------------- */
+
+/* Pack the canonical gauge field `links_dev` (device, complex128[V][4][3][3]) into `packed_dev`
+ * (device, qcd_links_bytes(lat, prec, recon) bytes) and register it as the links used by every
+ * later call at precision `prec`. Recon 18 folds 1/2 * eta * zeta into the stored links; recon 12
+ * stores the first two rows and the kernels rebuild the third as conj(row0 x row1) and apply
+ * the phases from the site coordinates. The caller keeps `packed_dev` alive. */
+QCD_API int qcd_load_links(qcd_lattice* lat, const void* links_dev, void* packed_dev, int prec, int recon,
+                   void* stream);
+
+/* ---- fields ------------------------------------------------------------------------------------ */
+
+/* canonical (device, complex128[V][3]) -> packed field of parity `parity` at `prec`. */
+QCD_API int qcd_pack_field(const qcd_lattice* lat, void* packed_dev, const void* canonical_dev, int parity,
+                   int prec, void* stream);
+/* packed -> canonical; writes only the sites of `parity`, leaves the other half untouched. */
+QCD_API int qcd_unpack_field(const qcd_lattice* lat, void* canonical_dev, const void* packed_dev, int parity,
+                     int prec, void* stream);
+
+/* ---- operators (paper §3 matrix-vector routine; §4 fmv / fmtv calls) ------------------------- */
+
+/* Half-lattice hop: out (parity out_parity) = D in (parity 1 - out_parity), packed fields at
+ * `prec`, using the links registered for `prec`. `out` is overwritten and must not alias `in`.
+ * With QCD_PREC_HALF the arithmetic is FP32 and the output is re-quantised per site. */
+QCD_API int qcd_dslash(const qcd_lattice* lat, void* out_dev, const void* in_dev, int out_parity, int prec,
+               void* stream);
+/* Same operator on nrhs right-hand sides at once (multi-RHS packed fields): every link is loaded
+ * once and applied to all nrhs vectors. 1 <= nrhs <= 16. */
+QCD_API int qcd_dslash_mrhs(const qcd_lattice* lat, void* out_dev, const void* in_dev, int nrhs, int out_parity,
+                    int prec, void* stream);
+/* Even-site normal operator: out_e = (m^2 - D_eo D_oe) in_e, packed even fields at `prec`.
+ * `tmp_dev` is caller scratch for one packed odd field (qcd_field_bytes(lat, prec) bytes).
+ * mass must be > 0. */
+QCD_API int qcd_mdagm(const qcd_lattice* lat, void* out_dev, const void* in_dev, double mass, int prec,
+              void* tmp_dev, void* stream);
+
+/* ---- solver (paper §4 congrad) --------------------------------------------------------------- */
+
+/* Solve A x_e = b_e to |b_e - A x_e| / |b_e| <= tol (true FP64 residual) and, when y_dev is not
+ * NULL, form y_o = D_oe x_e (the paper's "solution on the second half lattice").
+ *   x_dev, b_dev, y_dev : device canonical fields complex128[V][3]; only the even half of b is
+ *                         read; x is written on the even sites (odd half set to 0); y on the odd
+ *                         sites (even half set to 0).
+ *   workspace_dev       : device, qcd_workspace_bytes(lat, opts, 1) bytes.
+ *   opts                : NULL = defaults. prec_inner = DOUBLE runs plain FP64 CG; SINGLE/HALF run
+ *                         the mixed-precision CG with FP64 reliable updates (links for that
+ *                         precision and for DOUBLE must both be loaded).
+ *   info                : optional; filled on return.
+ * Synchronises `stream` before returning. Returns QCD_ERR_NOT_CONVERGED when max_iter runs out,
+ * QCD_ERR_BREAKDOWN when a CG scalar is non-finite or non-positive. */
+QCD_API int qcd_cg_solve(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, double tol, int max_iter,
+                 const qcd_solver_opts* opts, void* workspace_dev, void* y_dev, qcd_solve_info* info,
+                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCD_H */

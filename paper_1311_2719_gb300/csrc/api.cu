@@ -1,0 +1,266 @@
+// C-ABI entry points: argument validation, handle bookkeeping and error reporting around the
+// kernels of pack.cu, dslash.cu and cg.cu.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  return QCD_ERR_CUDA;
+}
+
+int launch_pack_links(const qcd_lattice*, const void*, void*, int, int, cudaStream_t);
+int launch_pack_field(const qcd_lattice*, void*, const void*, int, int, cudaStream_t);
+int launch_unpack_field(const qcd_lattice*, void*, const void*, int, int, cudaStream_t);
+int launch_dslash(const qcd_lattice*, void*, const void*, int, int, cudaStream_t);
+int launch_dslash_mrhs(const qcd_lattice*, void*, const void*, int, int, int, int, cudaStream_t);
+int launch_mdagm(const qcd_lattice*, void*, const void*, double, int, void*, cudaStream_t);
+size_t cg_workspace_bytes(const qcd_lattice*, int);
+int run_cg(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*,
+           qcd_solve_info*, cudaStream_t);
+
+static int invalid(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return QCD_ERR_INVALID_ARG;
+}
+
+static bool aligned(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+static bool valid_prec(int p) { return p == QCD_PREC_DOUBLE || p == QCD_PREC_SINGLE || p == QCD_PREC_HALF; }
+static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+static int check_dev_ptr(const void* p, const char* name) {
+  if (!p) return invalid("%s is NULL", name);
+  if (!aligned(p)) return invalid("%s is not 256-byte aligned", name);
+  return QCD_OK;
+}
+
+static int check_links(const qcd_lattice* lat, int prec) {
+  if (!valid_prec(prec)) return invalid("unknown precision %d", prec);
+  if (!lat->links[prec].ptr || !lat->links[prec].recon) {
+    set_error("no links loaded for precision %d (call qcd_load_links first)", prec);
+    return QCD_ERR_NO_LINKS;
+  }
+  return QCD_OK;
+}
+
+}  // namespace qcd
+
+using namespace qcd;
+
+extern "C" {
+
+const char* qcd_status_string(int s) {
+  switch (s) {
+    case QCD_OK: return "ok";
+    case QCD_ERR_INVALID_ARG: return "invalid argument";
+    case QCD_ERR_CUDA: return "CUDA error";
+    case QCD_ERR_NOT_CONVERGED: return "not converged";
+    case QCD_ERR_BREAKDOWN: return "solver breakdown";
+    case QCD_ERR_TIMEOUT: return "device wait timed out";
+    case QCD_ERR_UNSUPPORTED: return "unsupported";
+    case QCD_ERR_NO_LINKS: return "links not loaded";
+  }
+  return "unknown status";
+}
+
+const char* qcd_last_error(void) { return g_err; }
+
+const char* qcd_version(void) { return "qcd-gb300 0.1 (sm_103a)"; }
+
+int qcd_lattice_create(int L0, int L1, int L2, int L3, qcd_lattice** out) {
+  if (!out) return invalid("out is NULL");
+  *out = nullptr;
+  const int L[4] = {L0, L1, L2, L3};
+  long long V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (L[mu] < 2 || (L[mu] & 1)) return invalid("extent L%d = %d must be even and >= 2", mu, L[mu]);
+    V *= L[mu];
+  }
+  if (V >= (1ll << 31)) return invalid("volume %lld too large", V);
+  qcd_lattice* lat = new (std::nothrow) qcd_lattice();
+  if (!lat) return invalid("out of host memory");
+  for (int mu = 0; mu < 4; ++mu) lat->L[mu] = L[mu];
+  lat->V = V;
+  lat->Vh = V / 2;
+  lat->tbc = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  lat->device = dev;
+  *out = lat;
+  return QCD_OK;
+}
+
+int qcd_lattice_destroy(qcd_lattice* lat) {
+  delete lat;
+  return QCD_OK;
+}
+
+int qcd_lattice_set_tbc(qcd_lattice* lat, int sign) {
+  if (!lat) return invalid("lat is NULL");
+  if (sign != 1 && sign != -1) return invalid("tbc sign must be +1 or -1, got %d", sign);
+  if (sign != lat->tbc) {
+    lat->tbc = sign;
+    for (auto& l : lat->links) l = LinkSet{};
+  }
+  return QCD_OK;
+}
+
+int qcd_lattice_device(const qcd_lattice* lat) { return lat ? lat->device : -1; }
+
+size_t qcd_field_bytes(const qcd_lattice* lat, int prec) {
+  if (!lat || !valid_prec(prec)) return 0;
+  return field_bytes(prec, lat->Vh);
+}
+
+size_t qcd_links_bytes(const qcd_lattice* lat, int prec, int recon) {
+  if (!lat) return 0;
+  return links_bytes(prec, recon, lat->Vh);
+}
+
+void qcd_solver_opts_default(qcd_solver_opts* o) {
+  if (!o) return;
+  o->prec_inner = QCD_PREC_DOUBLE;
+  o->recon_inner = 18;
+  o->reliable_delta = 0.1;
+  o->reliable_interval = 100;
+  o->check_interval = 8;
+  o->use_graph = 1;
+  o->profile = 0;
+}
+
+size_t qcd_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts, int nrhs) {
+  if (!lat || nrhs != 1) return 0;
+  qcd_solver_opts o;
+  qcd_solver_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_prec(o.prec_inner)) return 0;
+  return cg_workspace_bytes(lat, o.prec_inner);
+}
+
+int qcd_load_links(qcd_lattice* lat, const void* links_dev, void* packed_dev, int prec, int recon, void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(links_dev, "links_dev")) return rc;
+  if (int rc = check_dev_ptr(packed_dev, "packed_dev")) return rc;
+  if (!valid_prec(prec)) return invalid("unknown precision %d", prec);
+  if (links_bytes(prec, recon, lat->Vh) == 0) {
+    set_error("precision %d with reconstruct-%d is not provided", prec, recon);
+    return QCD_ERR_UNSUPPORTED;
+  }
+  int rc = launch_pack_links(lat, links_dev, packed_dev, prec, recon, as_stream(stream));
+  if (rc) return rc;
+  lat->links[prec].ptr = packed_dev;
+  lat->links[prec].recon = recon;
+  return QCD_OK;
+}
+
+int qcd_pack_field(const qcd_lattice* lat, void* packed_dev, const void* canonical_dev, int parity, int prec,
+                   void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(packed_dev, "packed_dev")) return rc;
+  if (int rc = check_dev_ptr(canonical_dev, "canonical_dev")) return rc;
+  if (parity != QCD_EVEN && parity != QCD_ODD) return invalid("parity must be 0 or 1, got %d", parity);
+  if (!valid_prec(prec)) return invalid("unknown precision %d", prec);
+  return launch_pack_field(lat, packed_dev, canonical_dev, parity, prec, as_stream(stream));
+}
+
+int qcd_unpack_field(const qcd_lattice* lat, void* canonical_dev, const void* packed_dev, int parity, int prec,
+                     void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(packed_dev, "packed_dev")) return rc;
+  if (int rc = check_dev_ptr(canonical_dev, "canonical_dev")) return rc;
+  if (parity != QCD_EVEN && parity != QCD_ODD) return invalid("parity must be 0 or 1, got %d", parity);
+  if (!valid_prec(prec)) return invalid("unknown precision %d", prec);
+  return launch_unpack_field(lat, canonical_dev, packed_dev, parity, prec, as_stream(stream));
+}
+
+int qcd_dslash(const qcd_lattice* lat, void* out_dev, const void* in_dev, int out_parity, int prec, void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(out_dev, "out_dev")) return rc;
+  if (int rc = check_dev_ptr(in_dev, "in_dev")) return rc;
+  if (out_dev == in_dev) return invalid("out_dev must not alias in_dev");
+  if (out_parity != QCD_EVEN && out_parity != QCD_ODD) return invalid("out_parity must be 0 or 1");
+  if (int rc = check_links(lat, prec)) return rc;
+  return launch_dslash(lat, out_dev, in_dev, out_parity, prec, as_stream(stream));
+}
+
+int qcd_dslash_mrhs(const qcd_lattice* lat, void* out_dev, const void* in_dev, int nrhs, int out_parity, int prec,
+                    void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(out_dev, "out_dev")) return rc;
+  if (int rc = check_dev_ptr(in_dev, "in_dev")) return rc;
+  if (out_dev == in_dev) return invalid("out_dev must not alias in_dev");
+  if (nrhs < 1 || nrhs > kMaxRhs) return invalid("nrhs must be in [1, %d], got %d", kMaxRhs, nrhs);
+  if (out_parity != QCD_EVEN && out_parity != QCD_ODD) return invalid("out_parity must be 0 or 1");
+  if (int rc = check_links(lat, prec)) return rc;
+  int rb = 1;
+  while (rb * 2 <= nrhs && rb < (prec == QCD_PREC_DOUBLE ? 4 : 8)) rb *= 2;
+  return launch_dslash_mrhs(lat, out_dev, in_dev, nrhs, out_parity, prec, rb, as_stream(stream));
+}
+
+int qcd_mdagm(const qcd_lattice* lat, void* out_dev, const void* in_dev, double mass, int prec, void* tmp_dev,
+              void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(out_dev, "out_dev")) return rc;
+  if (int rc = check_dev_ptr(in_dev, "in_dev")) return rc;
+  if (int rc = check_dev_ptr(tmp_dev, "tmp_dev")) return rc;
+  if (tmp_dev == in_dev || tmp_dev == out_dev) return invalid("tmp_dev must not alias in_dev or out_dev");
+  if (!(mass > 0.0) || !std::isfinite(mass)) return invalid("mass must be finite and > 0, got %g", mass);
+  if (int rc = check_links(lat, prec)) return rc;
+  return launch_mdagm(lat, out_dev, in_dev, mass, prec, tmp_dev, as_stream(stream));
+}
+
+int qcd_cg_solve(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, double tol, int max_iter,
+                 const qcd_solver_opts* opts, void* workspace_dev, void* y_dev, qcd_solve_info* info, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (info) std::memset(info, 0, sizeof(*info));
+  auto done = [&](int rc) {
+    if (info) {
+      info->status = rc;
+      info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return rc;
+  };
+  if (!lat) return done(invalid("lat is NULL"));
+  if (int rc = check_dev_ptr(x_dev, "x_dev")) return done(rc);
+  if (int rc = check_dev_ptr(b_dev, "b_dev")) return done(rc);
+  if (int rc = check_dev_ptr(workspace_dev, "workspace_dev")) return done(rc);
+  if (y_dev && !aligned(y_dev)) return done(invalid("y_dev is not 256-byte aligned"));
+  if (x_dev == b_dev) return done(invalid("x_dev must not alias b_dev"));
+  if (!(mass > 0.0) || !std::isfinite(mass)) return done(invalid("mass must be finite and > 0, got %g", mass));
+  if (!(tol > 0.0) || !(tol < 1.0)) return done(invalid("tol must be in (0, 1), got %g", tol));
+  if (max_iter < 1) return done(invalid("max_iter must be >= 1, got %d", max_iter));
+  qcd_solver_opts o;
+  qcd_solver_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_prec(o.prec_inner)) return done(invalid("unknown inner precision %d", o.prec_inner));
+  if (o.reliable_delta < 0.0 || o.reliable_delta >= 1.0) return done(invalid("reliable_delta must be in [0, 1)"));
+  if (int rc = check_links(lat, QCD_PREC_DOUBLE)) return done(rc);
+  if (int rc = check_links(lat, o.prec_inner)) return done(rc);
+  if (lat->links[o.prec_inner].recon != o.recon_inner && o.prec_inner != QCD_PREC_DOUBLE) {
+    set_error("inner links loaded with reconstruct-%d, options ask for %d", lat->links[o.prec_inner].recon,
+              o.recon_inner);
+    return done(QCD_ERR_INVALID_ARG);
+  }
+  return done(run_cg(lat, x_dev, b_dev, mass, tol, max_iter, o, workspace_dev, y_dev, info, as_stream(stream)));
+}
+
+}  // extern "C"

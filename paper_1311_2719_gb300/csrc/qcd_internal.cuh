@@ -1,0 +1,505 @@
+// Internal types shared by the library's translation units: lattice geometry on the device,
+// complex colour algebra, packed field / link accessors for every precision, and the
+// deterministic block reduction used by the fused CG epilogues.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qcd.h"
+
+namespace qcd {
+
+constexpr int kBlock = 128;           // threads per block of the site kernels
+constexpr int kMaxPartials = 8192;    // per-reduction partial slots in the workspace
+constexpr int kMaxRhs = 16;
+
+// ------------------------------------------------------------------------------------------
+// Host-side handle.
+// ------------------------------------------------------------------------------------------
+struct LinkSet {
+  void* ptr = nullptr;  // caller-owned packed links
+  int recon = 0;        // 0 = not loaded
+};
+
+}  // namespace qcd
+
+struct qcd_lattice {
+  int L[4];
+  long long V;
+  long long Vh;
+  int tbc;
+  int device;
+  qcd::LinkSet links[3];  // indexed by precision
+};
+
+namespace qcd {
+
+// ------------------------------------------------------------------------------------------
+// Device geometry: even-odd index <-> coordinates and neighbours (the paper's iup/idn, computed).
+// ------------------------------------------------------------------------------------------
+struct Geom {
+  int L0, L1, L2, L3;
+  int Vh;
+  float tbc;  // +1 or -1
+};
+
+inline Geom make_geom(const qcd_lattice* lat) {
+  Geom g;
+  g.L0 = lat->L[0]; g.L1 = lat->L[1]; g.L2 = lat->L[2]; g.L3 = lat->L[3];
+  g.Vh = (int)lat->Vh;
+  g.tbc = (float)lat->tbc;
+  return g;
+}
+
+struct Site {
+  int x0, x1, x2, x3;
+  int lex;  // canonical index
+};
+
+// Coordinates of even-odd site k of parity `par`: the canonical pair (2k, 2k+1) shares x1..x3
+// and holds one site of each parity because L0 is even.
+__device__ __forceinline__ Site site_of(const Geom& g, int k, int par) {
+  Site s;
+  int j = 2 * k;
+  int t = j / g.L0;
+  int x0e = j - t * g.L0;
+  s.x1 = t % g.L1; t /= g.L1;
+  s.x2 = t % g.L2;
+  s.x3 = t / g.L2;
+  s.x0 = x0e + ((s.x1 + s.x2 + s.x3 + par) & 1);
+  s.lex = j + (s.x0 - x0e);
+  return s;
+}
+
+// Even-odd index of the forward (n + mu) and backward (n - mu) neighbours.
+__device__ __forceinline__ void neighbours(const Geom& g, const Site& s, int fwd[4], int bwd[4]) {
+  const int st1 = g.L0, st2 = g.L0 * g.L1, st3 = g.L0 * g.L1 * g.L2;
+  fwd[0] = (s.x0 == g.L0 - 1 ? s.lex - (g.L0 - 1) : s.lex + 1) >> 1;
+  bwd[0] = (s.x0 == 0 ? s.lex + (g.L0 - 1) : s.lex - 1) >> 1;
+  fwd[1] = (s.x1 == g.L1 - 1 ? s.lex - (g.L1 - 1) * st1 : s.lex + st1) >> 1;
+  bwd[1] = (s.x1 == 0 ? s.lex + (g.L1 - 1) * st1 : s.lex - st1) >> 1;
+  fwd[2] = (s.x2 == g.L2 - 1 ? s.lex - (g.L2 - 1) * st2 : s.lex + st2) >> 1;
+  bwd[2] = (s.x2 == 0 ? s.lex + (g.L2 - 1) * st2 : s.lex - st2) >> 1;
+  fwd[3] = (s.x3 == g.L3 - 1 ? s.lex - (g.L3 - 1) * st3 : s.lex + st3) >> 1;
+  bwd[3] = (s.x3 == 0 ? s.lex + (g.L3 - 1) * st3 : s.lex - st3) >> 1;
+}
+
+// eta_mu(n) * zeta_mu(n) of the link U_mu(n) (forward) and of U_mu(n - mu) (backward), as +-1.
+__device__ __forceinline__ float fwd_sign(const Geom& g, const Site& s, int mu) {
+  int e = 0;
+  if (mu >= 1) e += s.x0;
+  if (mu >= 2) e += s.x1;
+  if (mu >= 3) e += s.x2;
+  float sg = (e & 1) ? -1.f : 1.f;
+  if (mu == 3 && s.x3 == g.L3 - 1) sg *= g.tbc;
+  return sg;
+}
+__device__ __forceinline__ float bwd_sign(const Geom& g, const Site& s, int mu) {
+  // eta_mu(n - mu) = eta_mu(n); zeta of the link at n - mu is tbc when x3(n) == 0.
+  int e = 0;
+  if (mu >= 1) e += s.x0;
+  if (mu >= 2) e += s.x1;
+  if (mu >= 3) e += s.x2;
+  float sg = (e & 1) ? -1.f : 1.f;
+  if (mu == 3 && s.x3 == 0) sg *= g.tbc;
+  return sg;
+}
+
+// ------------------------------------------------------------------------------------------
+// Complex colour algebra in the compute type T (double or float).
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct cplx {
+  T re, im;
+};
+
+template <typename T>
+struct cvec3 {
+  cplx<T> c[3];
+};
+
+template <typename T>
+struct su3 {
+  cplx<T> e[3][3];
+};
+
+template <typename T>
+__device__ __forceinline__ void zero(cvec3<T>& v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v.c[a].re = v.c[a].im = T(0);
+}
+
+// acc += U x
+template <typename T>
+__device__ __forceinline__ void mul_add(cvec3<T>& acc, const su3<T>& U, const cvec3<T>& x) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      acc.c[a].re = fma(U.e[a][b].re, x.c[b].re, acc.c[a].re);
+      acc.c[a].re = fma(-U.e[a][b].im, x.c[b].im, acc.c[a].re);
+      acc.c[a].im = fma(U.e[a][b].re, x.c[b].im, acc.c[a].im);
+      acc.c[a].im = fma(U.e[a][b].im, x.c[b].re, acc.c[a].im);
+    }
+  }
+}
+
+// acc -= U^dagger x
+template <typename T>
+__device__ __forceinline__ void adj_mul_sub(cvec3<T>& acc, const su3<T>& U, const cvec3<T>& x) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      // conj(U_ba) x_b = (U_re - i U_im)(x_re + i x_im)
+      acc.c[a].re = fma(-U.e[b][a].re, x.c[b].re, acc.c[a].re);
+      acc.c[a].re = fma(-U.e[b][a].im, x.c[b].im, acc.c[a].re);
+      acc.c[a].im = fma(-U.e[b][a].re, x.c[b].im, acc.c[a].im);
+      acc.c[a].im = fma(U.e[b][a].im, x.c[b].re, acc.c[a].im);
+    }
+  }
+}
+
+// w = U x
+template <typename T>
+__device__ __forceinline__ cvec3<T> mul(const su3<T>& U, const cvec3<T>& x) {
+  cvec3<T> w;
+  zero(w);
+  mul_add(w, U, x);
+  return w;
+}
+
+// w = U^dagger x
+template <typename T>
+__device__ __forceinline__ cvec3<T> adj_mul(const su3<T>& U, const cvec3<T>& x) {
+  cvec3<T> w;
+  zero(w);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      w.c[a].re = fma(U.e[b][a].re, x.c[b].re, w.c[a].re);
+      w.c[a].re = fma(U.e[b][a].im, x.c[b].im, w.c[a].re);
+      w.c[a].im = fma(U.e[b][a].re, x.c[b].im, w.c[a].im);
+      w.c[a].im = fma(-U.e[b][a].im, x.c[b].re, w.c[a].im);
+    }
+  }
+  return w;
+}
+
+// acc += s * w
+template <typename T>
+__device__ __forceinline__ void axpy(cvec3<T>& acc, T s, const cvec3<T>& w) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc.c[a].re = fma(s, w.c[a].re, acc.c[a].re);
+    acc.c[a].im = fma(s, w.c[a].im, acc.c[a].im);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T norm2(const cvec3<T>& v) {
+  T s = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) s = fma(v.c[a].re, v.c[a].re, fma(v.c[a].im, v.c[a].im, s));
+  return s;
+}
+
+// Third row of an SU(3) matrix from the first two: c = conj(a x b).
+template <typename T>
+__device__ __forceinline__ void reconstruct_row2(su3<T>& U) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    // a_j b_k - a_k b_j
+    T re = U.e[0][j].re * U.e[1][k].re - U.e[0][j].im * U.e[1][k].im;
+    T im = U.e[0][j].re * U.e[1][k].im + U.e[0][j].im * U.e[1][k].re;
+    re = fma(-U.e[0][k].re, U.e[1][j].re, re);
+    re = fma(U.e[0][k].im, U.e[1][j].im, re);
+    im = fma(-U.e[0][k].re, U.e[1][j].im, im);
+    im = fma(-U.e[0][k].im, U.e[1][j].re, im);
+    U.e[2][i].re = re;
+    U.e[2][i].im = -im;
+  }
+}
+
+__device__ __forceinline__ float2 u32_to_float2(unsigned u) {
+  return __half22float2(__halves2half2(__ushort_as_half((unsigned short)(u & 0xffffu)),
+                                       __ushort_as_half((unsigned short)(u >> 16))));
+}
+__device__ __forceinline__ unsigned float2_to_u32(float a, float b) {
+  return (unsigned)__half_as_ushort(__float2half_rn(a)) | ((unsigned)__half_as_ushort(__float2half_rn(b)) << 16);
+}
+
+// ------------------------------------------------------------------------------------------
+// Packed fields. One parity, V/2 sites, structure of arrays.
+// ------------------------------------------------------------------------------------------
+template <int PREC>
+struct Field;
+
+template <>
+struct Field<QCD_PREC_DOUBLE> {
+  using T = double;
+  static constexpr int kElemsPerSite = 3;
+  double2* p;  // [3][Vh]
+  int Vh;
+  __device__ __forceinline__ cvec3<double> load(int k) const {
+    cvec3<double> v;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double2 d = __ldg(p + (size_t)a * Vh + k);
+      v.c[a].re = d.x; v.c[a].im = d.y;
+    }
+    return v;
+  }
+  __device__ __forceinline__ void store(int k, const cvec3<double>& v) const {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[(size_t)a * Vh + k] = make_double2(v.c[a].re, v.c[a].im);
+  }
+  static size_t bytes(long long Vh) { return (size_t)Vh * 3 * sizeof(double2); }
+};
+
+template <>
+struct Field<QCD_PREC_SINGLE> {
+  using T = float;
+  static constexpr int kElemsPerSite = 3;
+  float2* p;  // [3][Vh]
+  int Vh;
+  __device__ __forceinline__ cvec3<float> load(int k) const {
+    cvec3<float> v;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 d = __ldg(p + (size_t)a * Vh + k);
+      v.c[a].re = d.x; v.c[a].im = d.y;
+    }
+    return v;
+  }
+  __device__ __forceinline__ void store(int k, const cvec3<float>& v) const {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[(size_t)a * Vh + k] = make_float2(v.c[a].re, v.c[a].im);
+  }
+  static size_t bytes(long long Vh) { return (size_t)Vh * 3 * sizeof(float2); }
+};
+
+// 16 bytes per site: three half2 colour components scaled by a per-site float.
+template <>
+struct Field<QCD_PREC_HALF> {
+  using T = float;
+  static constexpr int kElemsPerSite = 1;
+  uint4* p;  // [Vh]
+  int Vh;
+  __device__ __forceinline__ cvec3<float> load(int k) const {
+    uint4 q = __ldg(p + k);
+    const float s = __uint_as_float(q.w);
+    cvec3<float> v;
+    const unsigned w[3] = {q.x, q.y, q.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 f = u32_to_float2(w[a]);
+      v.c[a].re = f.x * s; v.c[a].im = f.y * s;
+    }
+    return v;
+  }
+  __device__ __forceinline__ void store(int k, const cvec3<float>& v) const {
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) m = fmaxf(m, fmaxf(fabsf(v.c[a].re), fabsf(v.c[a].im)));
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+    unsigned w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) w[a] = float2_to_u32(v.c[a].re * inv, v.c[a].im * inv);
+    p[k] = make_uint4(w[0], w[1], w[2], __float_as_uint(m));
+  }
+  static size_t bytes(long long Vh) { return (size_t)Vh * sizeof(uint4); }
+};
+
+inline size_t field_bytes(int prec, long long Vh) {
+  switch (prec) {
+    case QCD_PREC_DOUBLE: return Field<QCD_PREC_DOUBLE>::bytes(Vh);
+    case QCD_PREC_SINGLE: return Field<QCD_PREC_SINGLE>::bytes(Vh);
+    case QCD_PREC_HALF: return Field<QCD_PREC_HALF>::bytes(Vh);
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// Packed links. Array of (parity, mu) blocks of V/2 sites each; link (par, mu, k) is U_mu at
+// even-odd site k of parity par. Recon 18 stores 1/2*eta*zeta*U; recon 12 stores rows 0, 1 of U.
+// ------------------------------------------------------------------------------------------
+template <int PREC, int RECON>
+struct Links;
+
+template <>
+struct Links<QCD_PREC_DOUBLE, 18> {
+  using T = double;
+  static constexpr bool kFolded = true;
+  const double2* p;  // [2][4][9][Vh]
+  int Vh;
+  __device__ __forceinline__ su3<double> load(int par, int mu, int k) const {
+    su3<double> U;
+    const double2* b = p + (size_t)(par * 4 + mu) * 9 * Vh + k;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      double2 d = __ldg(b + (size_t)e * Vh);
+      U.e[e / 3][e % 3].re = d.x; U.e[e / 3][e % 3].im = d.y;
+    }
+    return U;
+  }
+  static size_t bytes(long long Vh) { return (size_t)2 * 4 * 9 * Vh * sizeof(double2); }
+};
+
+template <>
+struct Links<QCD_PREC_SINGLE, 18> {
+  using T = float;
+  static constexpr bool kFolded = true;
+  const float2* p;  // [2][4][9][Vh]
+  int Vh;
+  __device__ __forceinline__ su3<float> load(int par, int mu, int k) const {
+    su3<float> U;
+    const float2* b = p + (size_t)(par * 4 + mu) * 9 * Vh + k;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      float2 d = __ldg(b + (size_t)e * Vh);
+      U.e[e / 3][e % 3].re = d.x; U.e[e / 3][e % 3].im = d.y;
+    }
+    return U;
+  }
+  static size_t bytes(long long Vh) { return (size_t)2 * 4 * 9 * Vh * sizeof(float2); }
+};
+
+template <>
+struct Links<QCD_PREC_SINGLE, 12> {
+  using T = float;
+  static constexpr bool kFolded = false;
+  const float4* p;  // [2][4][3][Vh]: (a0 a1) (a2 b0) (b1 b2)
+  int Vh;
+  __device__ __forceinline__ su3<float> load(int par, int mu, int k) const {
+    su3<float> U;
+    const float4* b = p + (size_t)(par * 4 + mu) * 3 * Vh + k;
+    float4 q0 = __ldg(b), q1 = __ldg(b + Vh), q2 = __ldg(b + 2 * (size_t)Vh);
+    U.e[0][0] = {q0.x, q0.y}; U.e[0][1] = {q0.z, q0.w};
+    U.e[0][2] = {q1.x, q1.y}; U.e[1][0] = {q1.z, q1.w};
+    U.e[1][1] = {q2.x, q2.y}; U.e[1][2] = {q2.z, q2.w};
+    reconstruct_row2(U);
+    return U;
+  }
+  static size_t bytes(long long Vh) { return (size_t)2 * 4 * 3 * Vh * sizeof(float4); }
+};
+
+template <>
+struct Links<QCD_PREC_HALF, 12> {
+  using T = float;
+  static constexpr bool kFolded = false;
+  const uint4* p;  // [2][4][Vh] halves of (a0 a1 a2 b0), then uint2 [2][4][Vh] halves of (b1 b2)
+  const uint2* q;
+  int Vh;
+  __device__ __forceinline__ su3<float> load(int par, int mu, int k) const {
+    su3<float> U;
+    const size_t o = (size_t)(par * 4 + mu) * Vh + k;
+    uint4 a = __ldg(p + o);
+    uint2 b = __ldg(q + o);
+    const unsigned w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      float2 f = u32_to_float2(w[e]);
+      U.e[e / 3][e % 3].re = f.x; U.e[e / 3][e % 3].im = f.y;
+    }
+    reconstruct_row2(U);
+    return U;
+  }
+  static size_t bytes(long long Vh) { return (size_t)2 * 4 * Vh * (sizeof(uint4) + sizeof(uint2)); }
+};
+
+inline size_t links_bytes(int prec, int recon, long long Vh) {
+  if (prec == QCD_PREC_DOUBLE && recon == 18) return Links<QCD_PREC_DOUBLE, 18>::bytes(Vh);
+  if (prec == QCD_PREC_SINGLE && recon == 18) return Links<QCD_PREC_SINGLE, 18>::bytes(Vh);
+  if (prec == QCD_PREC_SINGLE && recon == 12) return Links<QCD_PREC_SINGLE, 12>::bytes(Vh);
+  if (prec == QCD_PREC_HALF && recon == 12) return Links<QCD_PREC_HALF, 12>::bytes(Vh);
+  return 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// Deterministic reductions: per-block partial sums in FP64, the last block to finish sums the
+// partials in a fixed order (so results do not depend on block scheduling).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NV values over the block; thread 0 returns the totals in v.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sm[NV][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sm[j][warp] = v[j];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = lane < nw ? sm[j][lane] : 0.0;
+      v[j] = warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+// Write this block's partials; returns true in the block that finished last, after which
+// `tot` holds the grid-wide sums (valid in every thread of that block).
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last_block(double (&v)[NV], double* partials, unsigned* counter,
+                                                    double (&tot)[NV]) {
+  __shared__ bool am_last;
+  __shared__ double res[NV];
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) partials[(size_t)j * kMaxPartials + blockIdx.x] = v[j];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    s[j] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[j] += __ldcg(partials + (size_t)j * kMaxPartials + b);
+  }
+  block_sum<NV>(s);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) res[j] = s[j];
+    *counter = 0u;  // ready for the next launch
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) tot[j] = res[j];
+  return true;
+}
+
+// ------------------------------------------------------------------------------------------
+// Error plumbing (host).
+// ------------------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define QCD_CUDA(call)                                         \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return ::qcd::cuda_fail(e_, #call); \
+  } while (0)
+
+inline int grid_for(long long n, int block = kBlock) { return (int)((n + block - 1) / block); }
+
+}  // namespace qcd

@@ -1,0 +1,97 @@
+"""The C-ABI library loads, exports every symbol include/qcd.h declares, and validates arguments
+on the host (no GPU needed: these calls fail before any device work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"QCD_API\s+[\w\s\*]+?\b(qcd_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = _declared_symbols()
+    for must in ["qcd_lattice_create", "qcd_load_links", "qcd_dslash", "qcd_mdagm", "qcd_cg_solve"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1311_2719_gb300 import qcd as Q
+    lib = ctypes.CDLL(Q.LIB_PATH)
+    missing = [n for n in _declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding wraps exactly the declared surface
+    assert set(Q.SIGNATURES) == set(_declared_symbols())
+
+
+def test_lattice_validation_and_sizes():
+    from paper_1311_2719_gb300 import qcd as Q
+    for bad in [(3, 4, 4, 4), (4, 0, 4, 4), (4, 4, 4, 1), (4, 4, -2, 4)]:
+        with pytest.raises(Q.QcdError) as e:
+            Q.qcd_lattice_create(*bad)
+        assert e.value.status == Q.QCD_ERR_INVALID_ARG
+    h = Q.qcd_lattice_create(4, 4, 4, 8)
+    try:
+        Vh = 4 * 4 * 4 * 8 // 2
+        assert Q.qcd_field_bytes(h, Q.QCD_PREC_DOUBLE) == Vh * 48
+        assert Q.qcd_field_bytes(h, Q.QCD_PREC_SINGLE) == Vh * 24
+        assert Q.qcd_field_bytes(h, Q.QCD_PREC_HALF) == Vh * 16
+        assert Q.qcd_field_bytes(h, 7) == 0
+        assert Q.qcd_links_bytes(h, Q.QCD_PREC_DOUBLE, 18) == 2 * Vh * 4 * 144
+        assert Q.qcd_links_bytes(h, Q.QCD_PREC_SINGLE, 18) == 2 * Vh * 4 * 72
+        assert Q.qcd_links_bytes(h, Q.QCD_PREC_SINGLE, 12) == 2 * Vh * 4 * 48
+        assert Q.qcd_links_bytes(h, Q.QCD_PREC_HALF, 12) == 2 * Vh * 4 * 24
+        assert Q.qcd_links_bytes(h, Q.QCD_PREC_DOUBLE, 12) == 0
+        o = Q.qcd_solver_opts_default()
+        assert (o.prec_inner, o.recon_inner, o.reliable_interval) == (0, 18, 100)
+        assert Q.qcd_workspace_bytes(h, o) > 4 * Vh * 48
+        assert Q.qcd_lattice_set_tbc(h, 1) is None
+        with pytest.raises(Q.QcdError):
+            Q.qcd_lattice_set_tbc(h, 0)
+    finally:
+        Q.qcd_lattice_destroy(h)
+
+
+def test_calls_reject_bad_arguments_before_device_work():
+    from paper_1311_2719_gb300 import qcd as Q
+    h = Q.qcd_lattice_create(4, 4, 4, 4)
+    try:
+        fake = 1 << 20  # an aligned address that is never dereferenced: validation fails first
+        with pytest.raises(Q.QcdError) as e:
+            Q.qcd_dslash(h, fake, fake, 0, Q.QCD_PREC_DOUBLE)  # aliasing
+        assert e.value.status == Q.QCD_ERR_INVALID_ARG
+        with pytest.raises(Q.QcdError) as e:
+            Q.qcd_dslash(h, fake, fake + 256, 2, Q.QCD_PREC_DOUBLE)  # bad parity
+        assert e.value.status == Q.QCD_ERR_INVALID_ARG
+        with pytest.raises(Q.QcdError) as e:
+            Q.qcd_dslash(h, fake, fake + 256, 0, Q.QCD_PREC_DOUBLE)  # no links loaded
+        assert e.value.status == Q.QCD_ERR_NO_LINKS
+        with pytest.raises(Q.QcdError) as e:
+            Q.qcd_dslash(h, fake + 8, fake + 256, 0, Q.QCD_PREC_DOUBLE)  # misaligned
+        assert e.value.status == Q.QCD_ERR_INVALID_ARG
+        with pytest.raises(Q.QcdError) as e:
+            Q.qcd_dslash_mrhs(h, fake, fake + 256, 17, 0, Q.QCD_PREC_SINGLE)
+        assert e.value.status == Q.QCD_ERR_INVALID_ARG
+        with pytest.raises(Q.QcdError) as e:
+            Q.qcd_mdagm(h, fake, fake + 256, -0.1, Q.QCD_PREC_DOUBLE, fake + 512)
+        assert e.value.status == Q.QCD_ERR_INVALID_ARG
+        with pytest.raises(Q.QcdError) as e:
+            Q.qcd_load_links(h, fake, fake + 256, Q.QCD_PREC_DOUBLE, 12)
+        assert e.value.status == Q.QCD_ERR_UNSUPPORTED
+        o = Q.qcd_solver_opts_default()
+        for mass, tol, it in [(0.0, 1e-10, 10), (0.1, 0.0, 10), (0.1, 1e-10, 0), (float("nan"), 1e-10, 10)]:
+            rc, info = Q.qcd_cg_solve(h, fake, fake + 256, mass, tol, it, o, fake + 512, raise_on=())
+            assert rc == Q.QCD_ERR_INVALID_ARG and info["status"] == rc
+        rc, _ = Q.qcd_cg_solve(h, fake, fake + 256, 0.1, 1e-10, 10, o, fake + 512, raise_on=())
+        assert rc == Q.QCD_ERR_NO_LINKS
+    finally:
+        Q.qcd_lattice_destroy(h)

@@ -1,0 +1,135 @@
+"""GPU even-odd CG vs the FP64 oracle (solution, opposite-parity image, residuals, status codes)."""
+import numpy as np
+import pytest
+
+from oracle import staggered as S
+from paper_1311_2719_gb300 import inputs as I
+from paper_1311_2719_gb300 import qcd as Q
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from tests import gpu_helpers
+    return gpu_helpers
+
+
+def _kappa_bound(m):
+    # |D| <= 4 so the spectrum of A lies in [m^2, m^2 + 16]
+    return (m * m + 16.0) / (m * m)
+
+
+@pytest.mark.parametrize("dims,kind,m", [((4, 4, 4, 4), "haar", 0.1), ((2, 4, 6, 8), "haar", 0.1),
+                                         ((6, 6, 6, 6), "near_identity", 0.05), ((8, 8, 8, 8), "haar", 0.1)])
+def test_fp64_cg_matches_oracle(H, dims, kind, m):
+    U = I.make_links(dims, kind=kind, seed=1)
+    b = I.make_source(dims, seed=2)
+    ref = S.cg_solve(U, b, dims, m, tol=1e-10, max_iter=5000)
+    rig = H.Rig(dims, U, precs=["double"])
+    rc, info, x, y = rig.cg(b, m, tol=1e-10)
+    assert rc == Q.QCD_OK and info["converged"] == 1
+    assert info["true_rel_residual"] <= 1e-10
+    # an independent FP64 residual of the GPU solution, computed by the oracle
+    assert S.true_residual(U, x, b, dims, m) <= 1.01e-10
+    # same recursion in the same order: iteration counts agree closely, solutions to ~kappa * tol
+    assert abs(info["iterations"] - ref["iterations"]) <= 2
+    err = H.rel(x, ref["x"])
+    assert err <= _kappa_bound(m) * 1e-10 and err <= 1e-8, err
+    assert H.rel(y, ref["y"]) <= 1e-8
+    # y is D_oe x exactly as the half-lattice operator defines it
+    assert H.rel(y, S.dslash_parity(U, x, dims, 1)) <= 1e-12
+    assert np.all(x[S.parity(dims) == 1] == 0) and np.all(y[S.parity(dims) == 0] == 0)
+
+
+def test_free_field_converges_in_four_iterations(H):
+    dims = (4, 4, 4, 4)
+    U = I.make_links(dims, kind="unit")
+    rig = H.Rig(dims, U, precs=["double"])
+    rc, info, x, _ = rig.cg(I.make_source(dims, seed=2), 0.1, tol=1e-10, check_interval=1)
+    assert rc == Q.QCD_OK and info["iterations"] <= 5
+
+
+def test_graph_replay_equals_eager_bitwise(H):
+    dims = (6, 6, 6, 6)
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    rig = H.Rig(dims, U, precs=["double", "single12"])
+    for inner in ("double", "single12"):
+        _, i1, x1, y1 = rig.cg(b, 0.1, use_graph=1, check_interval=8, inner=inner)
+        _, i2, x2, y2 = rig.cg(b, 0.1, use_graph=0, check_interval=8, inner=inner)
+        assert i1["iterations"] == i2["iterations"]
+        assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
+        # deterministic reductions: a second run is bit-identical too
+        _, _, x3, _ = rig.cg(b, 0.1, use_graph=1, check_interval=8, inner=inner)
+        assert np.array_equal(x1, x3)
+
+
+@pytest.mark.parametrize("inner", ["single18", "single12", "half12"])
+@pytest.mark.parametrize("dims,m", [((8, 8, 8, 8), 0.1), ((6, 6, 6, 6), 0.02)])
+def test_mixed_precision_cg_reaches_fp64_residual(H, inner, dims, m):
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    ref = S.cg_solve(U, b, dims, m, tol=1e-12, max_iter=20000)
+    rig = H.Rig(dims, U, precs=["double", inner])
+    rc, info, x, y = rig.cg(b, m, tol=1e-10, inner=inner)
+    assert rc == Q.QCD_OK, info
+    assert info["true_rel_residual"] <= 1e-10 and info["reliable_updates"] >= 1
+    assert S.true_residual(U, x, b, dims, m) <= 1.01e-10
+    assert H.rel(x, ref["x"]) <= _kappa_bound(m) * 1e-10
+    assert H.rel(y, S.dslash_parity(U, x, dims, 1)) <= 1e-12
+
+
+def test_status_codes(H):
+    dims = (4, 4, 4, 4)
+    U = I.make_links(dims, kind="haar", seed=1)
+    rig = H.Rig(dims, U, precs=["double", "single12"])
+    b = I.make_source(dims, seed=2)
+    # max_iter exhausted
+    rc, info, _, _ = rig.cg(b, 0.1, max_iter=3, check_interval=1)
+    assert rc == Q.QCD_ERR_NOT_CONVERGED and info["iterations"] == 3 and not info["converged"]
+    # injected breakdown: a NaN in the source
+    bn = b.copy()
+    bn[0, 1] = np.nan
+    for inner in ("double", "single12"):
+        rc, info, _, _ = rig.cg(bn, 0.1, inner=inner)
+        assert rc == Q.QCD_ERR_BREAKDOWN
+    # zero source: x = 0 exactly, converged without iterating
+    rc, info, x, y = rig.cg(np.zeros_like(b), 0.1)
+    assert rc == Q.QCD_OK and info["iterations"] == 0 and not np.any(x) and not np.any(y)
+
+
+@pytest.mark.parametrize("kind,m", [("near_identity", 0.5), ("haar", 0.5), ("haar", 0.1), ("haar", 0.02),
+                                    ("near_identity", 0.02)])
+def test_full_size_16_4_fp64(H, kind, m):
+    """16^4, FP64 CG to 1e-10 at every mass of the workload; oracle solution where it is quick."""
+    dims = (16, 16, 16, 16)
+    U = I.make_links(dims, kind=kind, seed=1)
+    b = I.make_source(dims, seed=2)
+    rig = H.Rig(dims, U, precs=["double"])
+    rc, info, x, y = rig.cg(b, m, tol=1e-10)
+    assert rc == Q.QCD_OK and info["true_rel_residual"] <= 1e-10
+    assert S.true_residual(U, x, b, dims, m) <= 1.01e-10
+    if m >= 0.5:
+        ref = S.cg_solve(U, b, dims, m, tol=1e-10, max_iter=1000)
+        assert H.rel(x, ref["x"]) <= 1e-8
+
+
+@pytest.mark.parametrize("inner", ["single12", "half12"])
+def test_full_size_32_4_mixed(H, inner):
+    """32^4, m = 0.01: mixed CG reaches a true FP64 residual of 1e-10 (sampled oracle residual)."""
+    dims = (32, 32, 32, 32)
+    m = 0.01
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    rig = H.Rig(dims, U, precs=["double", inner])
+    rc, info, x, y = rig.cg(b, m, tol=1e-10, inner=inner, max_iter=40000)
+    assert rc == Q.QCD_OK, info
+    assert info["true_rel_residual"] <= 1e-10
+    # sampled FP64 residual by the oracle: |b - A x| at 2000 even sites relative to |b| there
+    rng = np.random.default_rng(0)
+    V = S.volume(dims)
+    cand = rng.choice(V, 6000, replace=False)
+    sites = cand[S.parity_of_sites(dims, cand) == 0][:2000]
+    r = b[sites] - S.mdagm_sites(U, x, dims, m, sites)
+    assert np.linalg.norm(r) / np.linalg.norm(b[sites]) <= 3e-10
