@@ -160,6 +160,23 @@ QCD_API int qcd_dslash_mrhs(const qcd_lattice* lat, void* out_dev, const void* i
 QCD_API int qcd_mdagm(const qcd_lattice* lat, void* out_dev, const void* in_dev, double mass, int prec,
               void* tmp_dev, void* stream);
 
+/* Same operator as qcd_mdagm, for callers that cannot allocate device memory. The paper has no
+ * counterpart: this exists because some host programs cannot obtain a scratch buffer to pass as
+ * `tmp_dev` — their device arrays are all placed by compiler data directives, or every byte of the
+ * GPU is owned and accounted for by another framework's memory pool, so calling cudaMalloc is not
+ * possible or not permitted. Here the intermediate odd-parity field lives in a 16 MiB array inside
+ * the library (a file-scope __device__ array that every GPU loading the library keeps until the
+ * process exits); the caller passes only `in_dev` and `out_dev`, and nothing is allocated.
+ *   Limit: qcd_field_bytes(lat, prec) must be <= 16 MiB (e.g. FP64 up to V/2 = 349525 sites,
+ *   24^4; FP32 and FP16 up to 32^4); larger lattices get QCD_ERR_INVALID_ARG.
+ *   The first call on each device looks up the array's device address with that device current;
+ *   make that first call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents (the operator overwrites
+ *   it completely before reading it). Calls whose executions overlap on the GPU — e.g. on two
+ *   streams at once — race on it; serialise them. */
+QCD_API int qcd_mdagm_noalloc(const qcd_lattice* lat, void* out_dev, const void* in_dev, double mass, int prec,
+                      void* stream);
+
 /* ---- solver (paper §4 congrad) --------------------------------------------------------------- */
 
 /* Solve A x_e = b_e to |b_e - A x_e| / |b_e| <= tol (true FP64 residual) and, when y_dev is not

@@ -1,0 +1,84 @@
+// qcd_mdagm_noalloc: the even-site normal operator with its intermediate odd-parity field kept in
+// a library-owned, statically sized device array instead of caller scratch.
+//
+// Some callers cannot hand the library a scratch buffer: host programs whose device arrays all
+// come from compiler data directives or from another framework's memory pool have no way to
+// call cudaMalloc (or are not allowed to, because that pool owns and accounts for every byte of
+// the GPU). This entry point lets them apply m^2 - D_eo D_oe with only their input and output.
+//
+// The scratch is a file-scope __device__ array of kNoAllocScratchBytes. Every GPU that loads the
+// library holds it until the process exits. Host code only ever sees a host-side stand-in for
+// the array's name, so its device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+#include <mutex>
+
+#include "dslash.cuh"
+
+namespace qcd {
+
+int launch_mdagm(const qcd_lattice*, void*, const void*, double, int, void*, cudaStream_t);
+void set_error(const char* fmt, ...);
+
+constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB: one packed odd field
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_mdagm_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_scratch_mutex;
+static void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_mdagm_scratch on `dev` (the current device). First use per device does the
+// lookup; later calls read the cached pointer.
+static int scratch_for_device(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal %d outside the supported range [0, %d)", dev, kMaxDevices);
+    return QCD_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_mdagm_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return QCD_OK;
+}
+
+}  // namespace qcd
+
+using namespace qcd;
+
+extern "C" int qcd_mdagm_noalloc(const qcd_lattice* lat, void* out_dev, const void* in_dev, double mass, int prec,
+                                 void* stream) {
+  if (!lat) { set_error("lat is NULL"); return QCD_ERR_INVALID_ARG; }
+  if (!out_dev || !in_dev) { set_error("out_dev and in_dev must not be NULL"); return QCD_ERR_INVALID_ARG; }
+  if (((uintptr_t)out_dev & 255u) || ((uintptr_t)in_dev & 255u)) {
+    set_error("out_dev and in_dev must be 256-byte aligned");
+    return QCD_ERR_INVALID_ARG;
+  }
+  if (out_dev == in_dev) { set_error("out_dev must not alias in_dev"); return QCD_ERR_INVALID_ARG; }
+  if (prec != QCD_PREC_DOUBLE && prec != QCD_PREC_SINGLE && prec != QCD_PREC_HALF) {
+    set_error("unknown precision %d", prec);
+    return QCD_ERR_INVALID_ARG;
+  }
+  if (!(mass > 0.0) || !(mass < 1e300)) { set_error("mass must be finite and > 0, got %g", mass); return QCD_ERR_INVALID_ARG; }
+  const size_t need = field_bytes(prec, lat->Vh);
+  if (need > kNoAllocScratchBytes) {
+    set_error("qcd_mdagm_noalloc: one packed field of this lattice needs %zu bytes at precision %d, above the "
+              "built-in scratch of %zu bytes; use qcd_mdagm with caller scratch", need, prec, kNoAllocScratchBytes);
+    return QCD_ERR_INVALID_ARG;
+  }
+  if (!lat->links[prec].ptr || !lat->links[prec].recon) {
+    set_error("no links loaded for precision %d (call qcd_load_links first)", prec);
+    return QCD_ERR_NO_LINKS;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  void* scratch = nullptr;
+  if (int rc = scratch_for_device(dev, &scratch)) return rc;
+  // The scratch is overwritten at every site by the first half-lattice hop before it is read,
+  // so nothing in it has to start at zero.
+  return launch_mdagm(lat, out_dev, in_dev, mass, prec, scratch, (cudaStream_t)stream);
+}

@@ -91,6 +91,7 @@ SIGNATURES = {
     "qcd_dslash": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "qcd_dslash_mrhs": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "qcd_mdagm": (_i, [_vp, _vp, _vp, _d, _i, _vp, _vp]),
+    "qcd_mdagm_noalloc": (_i, [_vp, _vp, _vp, _d, _i, _vp]),
     "qcd_cg_solve": (_i, [_vp, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp, _vp,
                           ctypes.POINTER(qcd_solve_info), _vp]),
 }
@@ -208,6 +209,13 @@ def qcd_dslash_mrhs(lat, out_dev, in_dev, nrhs, out_parity, prec, stream=None):
 def qcd_mdagm(lat, out_dev, in_dev, mass, prec, tmp_dev, stream=None):
     return _check(_lib.qcd_mdagm(lat, _ptr(out_dev), _ptr(in_dev), float(mass), prec, _ptr(tmp_dev),
                                  _stream(stream)), "qcd_mdagm")
+
+
+def qcd_mdagm_noalloc(lat, out_dev, in_dev, mass, prec, stream=None):
+    """qcd_mdagm without caller scratch: the library's built-in 16 MiB device array holds the
+    intermediate field, for callers that cannot allocate device memory."""
+    return _check(_lib.qcd_mdagm_noalloc(lat, _ptr(out_dev), _ptr(in_dev), float(mass), prec, _stream(stream)),
+                  "qcd_mdagm_noalloc")
 
 
 def qcd_cg_solve(lat, x_dev, b_dev, mass, tol, max_iter, opts, workspace_dev, y_dev=None, stream=None,
