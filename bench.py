@@ -46,6 +46,13 @@ WORKLOADS = {
                           desc="staggered 32^4 Haar, m=0.01, mixed CG: FP32 recon-12 inner, FP64 reliable updates"),
     "cg32_half12": dict(dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="half12",
                         desc="staggered 32^4 Haar, m=0.01, mixed CG: FP16+scale recon-12 inner, FP64 reliable updates"),
+    "mrhs24_single12": dict(kind_solve="mrhs", dims=(24, 24, 24, 24), kind="haar", mass=0.05, tol=1e-10,
+                            inner="single12", nrhs=16,
+                            desc="staggered 24^4 Haar, m=0.05, 16 RHS in one multi-RHS CG: FP32 recon-12 inner, "
+                                 "FP64 reliable updates"),
+    "batch64_single12": dict(kind_solve="batched", n=64, tol=1e-10, inner="single12",
+                             desc="64 independent staggered lattices {4^4,6^4,8^4,8^3x16}, m in [0.02,0.5], one "
+                                  "persistent clustered CG launch: FP32 recon-12 inner, FP64 reliable updates"),
 }
 DEFAULT_WORKLOAD = "cg16_fp64"
 PRECS = {"double": (0, 18), "single18": (1, 18), "single12": (1, 12), "half12": (2, 12)}
@@ -279,6 +286,164 @@ def run_gpu(args, wl):
     return out if rank == 0 else None
 
 
+def run_gpu_batched(args, wl):
+    """Multi-RHS (one lattice, nrhs sources) or multi-lattice (one persistent launch) workloads.
+
+    One step = pack every lattice's links (FP64 + inner precision) and run the batched mixed
+    solve. Reported beside: the same problems solved one by one with plain FP64 CG on the GPU
+    (time and the speedup of the batched mixed solve over it).
+    """
+    import torch
+
+    from paper_1311_2719_gb300 import inputs as I
+    from paper_1311_2719_gb300 import qcd as Q
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    inner = wl["inner"]
+    prec_in, recon_in = PRECS[inner]
+    tol = wl["tol"]
+    stream = torch.cuda.Stream()
+    if wl["kind_solve"] == "mrhs":
+        specs = [(wl["dims"], wl["mass"], 1, None)]
+        nrhs = wl["nrhs"]
+    else:
+        specs = I.make_lattice_batch(wl["n"], seed=4)
+        nrhs = 1
+    lats, U_dev, b_dev, x_dev, packed = [], [], [], [], []
+    for dims, m, ls, ss in specs:
+        lat = Q.Lattice(dims)
+        lats.append(lat)
+        U_dev.append(torch.from_numpy(I.make_links(dims, kind="haar", seed=ls)).cuda())
+        if nrhs > 1:
+            b_dev.append(torch.from_numpy(I.make_sources(dims, nrhs, first_seed=2)).cuda())
+        else:
+            b_dev.append(torch.from_numpy(I.make_source(dims, seed=ss)).cuda())
+        x_dev.append(torch.zeros_like(b_dev[-1]))
+        packed.append([(p, r, lat.empty_bytes(Q.qcd_links_bytes(lat.handle, p, r))) for p, r in
+                       sorted({(0, 18), (prec_in, recon_in)})])
+    masses = [s[1] for s in specs]
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner, opts.recon_inner = prec_in, recon_in
+    if wl["kind_solve"] == "mrhs":
+        ws = lats[0].workspace(opts, nrhs)
+    else:
+        ws = torch.empty(Q.qcd_workspace_bytes_batched([l.handle for l in lats], opts), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def load_links():
+        n = 0
+        for lat, Ud, pk in zip(lats, U_dev, packed):
+            for p, r, buf in pk:
+                Q.qcd_load_links(lat.handle, Ud, buf, p, r, stream)
+                n += 1
+        return n
+
+    def step():
+        with torch.cuda.stream(stream):
+            n = load_links()
+            if wl["kind_solve"] == "mrhs":
+                rc, infos = Q.qcd_cg_solve_mrhs(lats[0].handle, nrhs, x_dev[0], b_dev[0], masses[0], tol, 100000, opts,
+                                                ws, None, stream=stream)
+                vh = [lats[0].Vh] * nrhs
+            else:
+                rc, infos = Q.qcd_cg_solve_batched([l.handle for l in lats], x_dev, b_dev, None, masses, tol, 100000,
+                                                   opts, ws, stream=stream)
+                vh = [l.Vh for l in lats]
+        if rc != Q.QCD_OK:
+            raise RuntimeError(f"batched solve failed: {Q.qcd_status_string(rc)}")
+        flops = sum(FLOP_PER_SITE * v * _half_dslash_count(i) for v, i in zip(vh, infos))
+        return flops, infos, n + sum(i["kernel_launches"] for i in infos)
+
+    def timed(fn, n):
+        ms, outs = [], []
+        for _ in range(n):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs.append(fn())
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, outs
+
+    if args.tune:
+        with torch.cuda.stream(stream):
+            load_links()
+            if wl["kind_solve"] == "mrhs":
+                Q.qcd_tune_mrhs(lats[0].handle, nrhs, x_dev[0], b_dev[0], masses[0], opts, ws, stream=stream)
+            else:
+                Q.qcd_tune_batched([l.handle for l in lats], x_dev, b_dev, masses, tol, 100000, opts, ws, stream=stream)
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    proc, cpath = _clock_sampler(uuid)
+    time.sleep(0.3)
+    ms, outs = timed(step, args.steps)
+    clocks = _clock_summary(proc, cpath)
+
+    # the same problems, one by one, with plain FP64 CG on the GPU
+    o64 = Q.qcd_solver_opts_default()
+    def fp64_step():
+        with torch.cuda.stream(stream):
+            for lat, Ud, pk in zip(lats, U_dev, packed):
+                Q.qcd_load_links(lat.handle, Ud, pk[0][2], 0, 18, stream)
+            for j, (lat, m) in enumerate(zip(lats, masses)):
+                ws64 = lat.workspace(o64)
+                for r in range(nrhs):
+                    bj = b_dev[j][r] if nrhs > 1 else b_dev[j]
+                    xj = x_dev[j][r] if nrhs > 1 else x_dev[j]
+                    rc, _ = Q.qcd_cg_solve(lat.handle, xj, bj, m, tol, 100000, o64, ws64, None, stream=stream)
+                    if rc != Q.QCD_OK:
+                        raise RuntimeError("FP64 reference solve failed")
+        return 0
+    fp64_step()
+    ms64, _ = timed(fp64_step, max(1, min(args.steps, 3)))
+
+    tot = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
+    fl = torch.tensor([float(sum(o[0] for o in outs))], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        dist.all_reduce(fl, op=dist.ReduceOp.SUM)
+    value = fl.item() / (tot.item() * 1e-3) / 1e9
+    infos = outs[-1][1]
+    t_batched = sum(ms) / args.steps
+    t_fp64 = sum(ms64) / len(ms64)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_batched, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[inner], "data": "synthetic (seeded Haar SU(3) links, Gaussian sources)",
+        "config": {"workload": wl["desc"], "problems": len(specs) * nrhs, "tol": tol, "inner": inner,
+                   "parallelism": f"replicas x{world} (no sharding)",
+                   "l2": "flushed before every step (512 MB write, outside the timed events)",
+                   "step": "qcd_load_links for every lattice + " +
+                           ("qcd_cg_solve_mrhs" if nrhs > 1 else "qcd_cg_solve_batched (one persistent launch)")},
+        "cg": {"time_to_solution_ms": round(t_batched, 4),
+               "max_iterations": max(i["iterations"] for i in infos),
+               "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
+               "reliable_updates": sum(i["reliable_updates"] for i in infos),
+               "plain_fp64_gpu_cg_ms": round(t_fp64, 4),
+               "speedup_vs_plain_fp64_gpu_cg": round(t_fp64 / t_batched, 3)},
+        "gpu_launches": int(sum(o[2] for o in outs)),
+        "clocks": clocks,
+    }
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
 def _oracle_sample(wl, iters, U=None, b=None):
     """Time the FP64 oracle CG, as it stands, for `iters` iterations of the workload."""
     from oracle import staggered as S
@@ -343,11 +508,17 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=64, help="oracle CG iterations timed for cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=12, help="oracle CG iterations per --impl reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="run the autotuner before the batched workloads")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     wl = WORKLOADS[args.workload]
-    out = run_reference(args, wl) if args.impl == "reference" else run_gpu(args, wl)
+    if args.impl == "reference":
+        out = run_reference(args, wl)
+    elif wl.get("kind_solve") in ("mrhs", "batched"):
+        out = run_gpu_batched(args, wl)
+    else:
+        out = run_gpu(args, wl)
     if out is not None:
         print(json.dumps(out), flush=True)
 

@@ -76,6 +76,12 @@ typedef struct {
   int use_graph;         /* replay each k-iteration chunk as a CUDA graph (1)                     */
   int profile;           /* record CUDA events around every operator launch of the iteration (0);
                             profiled chunks run as direct launches, not graph replays         */
+  int rhs_block;         /* multi-RHS solves: right-hand sides per register block, 1/2/4/8/16;
+                            0 = the tuned value if qcd_tune_mrhs recorded one, else a default   */
+  int cluster_size;      /* batched solves: thread blocks per cluster (one cluster per lattice
+                            at a time), 1/2/4/8/16; 0 = tuned value or 4                        */
+  int block_size;        /* batched solves: threads per block, multiple of 32 <= 256; 0 = tuned
+                            value or 256                                                        */
 } qcd_solver_opts;
 
 /* What a solve reports. */
@@ -119,7 +125,8 @@ QCD_API size_t qcd_field_bytes(const qcd_lattice* lat, int prec);
 /* Bytes of the packed gauge field at (prec, recon). Supported: DOUBLE/18, SINGLE/18, SINGLE/12,
  * HALF/12. 0 on an unsupported pair. */
 QCD_API size_t qcd_links_bytes(const qcd_lattice* lat, int prec, int recon);
-/* Bytes of the device workspace qcd_cg_solve needs for these options (nrhs = 1). */
+/* Bytes of the device workspace qcd_cg_solve (nrhs = 1) or qcd_cg_solve_mrhs (1 <= nrhs <= 16)
+ * needs for these options; 0 on a bad argument. */
 QCD_API size_t qcd_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts, int nrhs);
 
 QCD_API void qcd_solver_opts_default(qcd_solver_opts* opts);
@@ -194,6 +201,57 @@ QCD_API int qcd_mdagm_noalloc(const qcd_lattice* lat, void* out_dev, const void*
 QCD_API int qcd_cg_solve(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, double tol, int max_iter,
                  const qcd_solver_opts* opts, void* workspace_dev, void* y_dev, qcd_solve_info* info,
                  void* stream);
+
+/* nrhs independent solves A x_r = b_r on one lattice in one set of launches: every link the
+ * operator loads is applied to a register block of right-hand sides (opts->rhs_block), each RHS
+ * keeps its own CG scalars and stops on its own (the batched-RHS form of the paper's congrad).
+ *   x_dev, b_dev, y_dev : nrhs canonical fields back to back, complex128[nrhs][V][3] (y nullable).
+ *   workspace_dev       : qcd_workspace_bytes(lat, opts, nrhs) bytes.
+ *   info                : optional array of nrhs entries; the launch/profiling counters are
+ *                         reported on entry 0.
+ * 1 <= nrhs <= 16. Returns QCD_OK when every RHS converged, else the first failing status
+ * (QCD_ERR_BREAKDOWN takes precedence). Synchronises `stream` before returning. */
+QCD_API int qcd_cg_solve_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, double mass, double tol,
+                      int max_iter, const qcd_solver_opts* opts, void* workspace_dev, void* y_dev,
+                      qcd_solve_info* info, void* stream);
+
+/* Bytes of the device workspace qcd_cg_solve_batched needs for these n lattices (0 on a bad
+ * argument). */
+QCD_API size_t qcd_workspace_bytes_batched(int n, qcd_lattice* const lats[], const qcd_solver_opts* opts);
+
+/* n independent solves A_i x_i = b_i on n lattices of any sizes and masses, in ONE persistent
+ * launch (the paper's congrad applied to a batch): each thread-block cluster takes the next
+ * lattice from a device work queue (longest expected solve first) and runs its whole CG there,
+ * reliable updates and the final y / true residual included, with cluster-scope reductions and
+ * no host round trip. With opts->use_graph and a non-default stream the launch is replayed from
+ * a CUDA graph.
+ *   lats[i] : links loaded at QCD_PREC_DOUBLE and at opts->prec_inner (same recon for all i).
+ *   x[i], b[i], y[i] : device canonical fields of lattice i (y and its entries nullable).
+ *   mass[i] : host array, > 0.   info : optional host array of n entries.
+ * Synchronises `stream`. Returns QCD_OK when every lattice converged, else the first failing
+ * status (QCD_ERR_BREAKDOWN first). */
+QCD_API int qcd_cg_solve_batched(int n, qcd_lattice* const lats[], void* const x[], const void* const b[],
+                         void* const y[], const double mass[], double tol, int max_iter,
+                         const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info info[], void* stream);
+
+/* ---- autotuning of launch shapes (no counterpart in the paper) ------------------------------ */
+
+/* Time the multi-RHS solver's operator launches (CUDA events over a 24-iteration run of the real
+ * solve on the caller's buffers, the same arguments as qcd_cg_solve_mrhs) for each register block
+ * of right-hand sides, store the fastest in the in-process table used when opts->rhs_block == 0,
+ * append it to `cache_path` (nullable) and return it in *best_rhs_block. x_dev is overwritten. */
+QCD_API int qcd_tune_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, double mass,
+                  const qcd_solver_opts* opts, void* workspace_dev, const char* cache_path, int* best_rhs_block,
+                  void* stream);
+/* Time whole batched solves (same arguments as qcd_cg_solve_batched, y omitted) for every
+ * (cluster size in {1,2,4,8,16}, block size in {128,256}) that fits; keep the fastest for
+ * opts->cluster_size == 0 / opts->block_size == 0, append it to `cache_path` (nullable). */
+QCD_API int qcd_tune_batched(int n, qcd_lattice* const lats[], void* const x[], const void* const b[],
+                     const double mass[], double tol, int max_iter, const qcd_solver_opts* opts,
+                     void* workspace_dev, const char* cache_path, int* best_cluster, int* best_block,
+                     void* stream);
+/* Load tuned entries written by the two calls above (missing file = nothing to load). */
+QCD_API int qcd_tune_load(const char* cache_path);
 
 #ifdef __cplusplus
 }

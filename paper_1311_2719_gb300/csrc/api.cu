@@ -31,9 +31,14 @@ int launch_unpack_field(const qcd_lattice*, void*, const void*, int, int, cudaSt
 int launch_dslash(const qcd_lattice*, void*, const void*, int, int, cudaStream_t);
 int launch_dslash_mrhs(const qcd_lattice*, void*, const void*, int, int, int, int, cudaStream_t);
 int launch_mdagm(const qcd_lattice*, void*, const void*, double, int, void*, cudaStream_t);
-size_t cg_workspace_bytes(const qcd_lattice*, int);
+size_t cg_workspace_bytes(const qcd_lattice*, int, int);
 int run_cg(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*,
            qcd_solve_info*, cudaStream_t);
+size_t batch_workspace_bytes(int, const qcd_lattice* const*, int);
+int run_cg_batched(int, qcd_lattice* const*, void* const*, const void* const*, void* const*, const double*, double, int,
+                   const qcd_solver_opts&, void*, qcd_solve_info*, cudaStream_t);
+int run_cg_mrhs(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*,
+                qcd_solve_info*, cudaStream_t);
 
 static int invalid(const char* fmt, ...) {
   va_list ap;
@@ -145,15 +150,18 @@ void qcd_solver_opts_default(qcd_solver_opts* o) {
   o->check_interval = 8;
   o->use_graph = 1;
   o->profile = 0;
+  o->rhs_block = 0;
+  o->cluster_size = 0;
+  o->block_size = 0;
 }
 
 size_t qcd_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts, int nrhs) {
-  if (!lat || nrhs != 1) return 0;
+  if (!lat || nrhs < 1 || nrhs > kMaxRhs) return 0;
   qcd_solver_opts o;
   qcd_solver_opts_default(&o);
   if (opts) o = *opts;
   if (!valid_prec(o.prec_inner)) return 0;
-  return cg_workspace_bytes(lat, o.prec_inner);
+  return cg_workspace_bytes(lat, o.prec_inner, nrhs);
 }
 
 int qcd_load_links(qcd_lattice* lat, const void* links_dev, void* packed_dev, int prec, int recon, void* stream) {
@@ -228,6 +236,41 @@ int qcd_mdagm(const qcd_lattice* lat, void* out_dev, const void* in_dev, double 
   return launch_mdagm(lat, out_dev, in_dev, mass, prec, tmp_dev, as_stream(stream));
 }
 
+}  // extern "C"
+
+namespace qcd {
+// Shared argument checks of the solver entry points; fills `o` with the effective options.
+static int check_solve_args(const qcd_lattice* lat, void* x_dev, const void* b_dev, void* workspace_dev, void* y_dev,
+                            double mass, double tol, int max_iter, const qcd_solver_opts* opts, qcd_solver_opts& o) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(x_dev, "x_dev")) return rc;
+  if (int rc = check_dev_ptr(b_dev, "b_dev")) return rc;
+  if (int rc = check_dev_ptr(workspace_dev, "workspace_dev")) return rc;
+  if (y_dev && !aligned(y_dev)) return invalid("y_dev is not 256-byte aligned");
+  if (x_dev == b_dev) return invalid("x_dev must not alias b_dev");
+  if (!(mass > 0.0) || !std::isfinite(mass)) return invalid("mass must be finite and > 0, got %g", mass);
+  if (!(tol > 0.0) || !(tol < 1.0)) return invalid("tol must be in (0, 1), got %g", tol);
+  if (max_iter < 1) return invalid("max_iter must be >= 1, got %d", max_iter);
+  qcd_solver_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_prec(o.prec_inner)) return invalid("unknown inner precision %d", o.prec_inner);
+  if (o.reliable_delta < 0.0 || o.reliable_delta >= 1.0) return invalid("reliable_delta must be in [0, 1)");
+  if (o.rhs_block != 0 && o.rhs_block != 1 && o.rhs_block != 2 && o.rhs_block != 4 && o.rhs_block != 8 &&
+      o.rhs_block != 16)
+    return invalid("rhs_block must be 0, 1, 2, 4, 8 or 16, got %d", o.rhs_block);
+  if (int rc = check_links(lat, QCD_PREC_DOUBLE)) return rc;
+  if (int rc = check_links(lat, o.prec_inner)) return rc;
+  if (o.prec_inner != QCD_PREC_DOUBLE && lat->links[o.prec_inner].recon != o.recon_inner) {
+    set_error("inner links loaded with reconstruct-%d, options ask for %d", lat->links[o.prec_inner].recon,
+              o.recon_inner);
+    return QCD_ERR_INVALID_ARG;
+  }
+  return QCD_OK;
+}
+}  // namespace qcd
+
+extern "C" {
+
 int qcd_cg_solve(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, double tol, int max_iter,
                  const qcd_solver_opts* opts, void* workspace_dev, void* y_dev, qcd_solve_info* info, void* stream) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -239,13 +282,63 @@ int qcd_cg_solve(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, 
     }
     return rc;
   };
-  if (!lat) return done(invalid("lat is NULL"));
-  if (int rc = check_dev_ptr(x_dev, "x_dev")) return done(rc);
-  if (int rc = check_dev_ptr(b_dev, "b_dev")) return done(rc);
+  qcd_solver_opts o;
+  if (int rc = check_solve_args(lat, x_dev, b_dev, workspace_dev, y_dev, mass, tol, max_iter, opts, o)) return done(rc);
+  return done(run_cg(lat, x_dev, b_dev, mass, tol, max_iter, o, workspace_dev, y_dev, info, as_stream(stream)));
+}
+
+int qcd_cg_solve_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, double mass, double tol,
+                      int max_iter, const qcd_solver_opts* opts, void* workspace_dev, void* y_dev,
+                      qcd_solve_info* info, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int n_info = (nrhs >= 1 && nrhs <= kMaxRhs) ? nrhs : 1;
+  if (info) std::memset(info, 0, sizeof(*info) * n_info);
+  auto done = [&](int rc) {
+    if (info) {
+      const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      for (int r = 0; r < n_info; ++r) {
+        if (rc != QCD_OK && info[r].status == QCD_OK && info[r].iterations == 0) info[r].status = rc;
+        info[r].seconds = sec;
+      }
+    }
+    return rc;
+  };
+  if (nrhs < 1 || nrhs > kMaxRhs) return done(invalid("nrhs must be in [1, %d], got %d", kMaxRhs, nrhs));
+  qcd_solver_opts o;
+  if (int rc = check_solve_args(lat, x_dev, b_dev, workspace_dev, y_dev, mass, tol, max_iter, opts, o)) return done(rc);
+  return done(run_cg_mrhs(lat, nrhs, x_dev, b_dev, mass, tol, max_iter, o, workspace_dev, y_dev, info,
+                          as_stream(stream)));
+}
+
+size_t qcd_workspace_bytes_batched(int n, qcd_lattice* const lats[], const qcd_solver_opts* opts) {
+  if (n < 1 || !lats) return 0;
+  for (int i = 0; i < n; ++i)
+    if (!lats[i]) return 0;
+  qcd_solver_opts o;
+  qcd_solver_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_prec(o.prec_inner)) return 0;
+  return batch_workspace_bytes(n, (const qcd_lattice* const*)lats, o.prec_inner);
+}
+
+int qcd_cg_solve_batched(int n, qcd_lattice* const lats[], void* const x[], const void* const b[], void* const y[],
+                         const double mass[], double tol, int max_iter, const qcd_solver_opts* opts,
+                         void* workspace_dev, qcd_solve_info info[], void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (info && n > 0) std::memset(info, 0, sizeof(*info) * n);
+  auto done = [&](int rc) {
+    if (info && n > 0) {
+      const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      for (int i = 0; i < n; ++i) {
+        if (rc != QCD_OK && info[i].status == QCD_OK && info[i].iterations == 0) info[i].status = rc;
+        info[i].seconds = sec;
+      }
+    }
+    return rc;
+  };
+  if (n < 1) return done(invalid("n must be >= 1, got %d", n));
+  if (!lats || !x || !b || !mass) return done(invalid("lats, x, b and mass must not be NULL"));
   if (int rc = check_dev_ptr(workspace_dev, "workspace_dev")) return done(rc);
-  if (y_dev && !aligned(y_dev)) return done(invalid("y_dev is not 256-byte aligned"));
-  if (x_dev == b_dev) return done(invalid("x_dev must not alias b_dev"));
-  if (!(mass > 0.0) || !std::isfinite(mass)) return done(invalid("mass must be finite and > 0, got %g", mass));
   if (!(tol > 0.0) || !(tol < 1.0)) return done(invalid("tol must be in (0, 1), got %g", tol));
   if (max_iter < 1) return done(invalid("max_iter must be >= 1, got %d", max_iter));
   qcd_solver_opts o;
@@ -253,14 +346,25 @@ int qcd_cg_solve(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, 
   if (opts) o = *opts;
   if (!valid_prec(o.prec_inner)) return done(invalid("unknown inner precision %d", o.prec_inner));
   if (o.reliable_delta < 0.0 || o.reliable_delta >= 1.0) return done(invalid("reliable_delta must be in [0, 1)"));
-  if (int rc = check_links(lat, QCD_PREC_DOUBLE)) return done(rc);
-  if (int rc = check_links(lat, o.prec_inner)) return done(rc);
-  if (lat->links[o.prec_inner].recon != o.recon_inner && o.prec_inner != QCD_PREC_DOUBLE) {
-    set_error("inner links loaded with reconstruct-%d, options ask for %d", lat->links[o.prec_inner].recon,
-              o.recon_inner);
-    return done(QCD_ERR_INVALID_ARG);
+  int dev = -1;
+  cudaGetDevice(&dev);
+  int recon0 = 0;
+  for (int i = 0; i < n; ++i) {
+    const qcd_lattice* lat = lats[i];
+    if (!lat) return done(invalid("lats[%d] is NULL", i));
+    if (lat->device != dev) return done(invalid("lats[%d] belongs to device %d, current device is %d", i, lat->device, dev));
+    if (int rc = check_dev_ptr(x[i], "x[i]")) return done(rc);
+    if (int rc = check_dev_ptr(b[i], "b[i]")) return done(rc);
+    if (y && y[i] && !aligned(y[i])) return done(invalid("y[%d] is not 256-byte aligned", i));
+    if (x[i] == b[i]) return done(invalid("x[%d] must not alias b[%d]", i, i));
+    if (!(mass[i] > 0.0) || !std::isfinite(mass[i])) return done(invalid("mass[%d] must be finite and > 0", i));
+    if (int rc = check_links(lat, QCD_PREC_DOUBLE)) return done(rc);
+    if (int rc = check_links(lat, o.prec_inner)) return done(rc);
+    if (i == 0) recon0 = lat->links[o.prec_inner].recon;
+    if (lat->links[o.prec_inner].recon != recon0)
+      return done(invalid("every lattice must load the inner links with the same reconstruction"));
   }
-  return done(run_cg(lat, x_dev, b_dev, mass, tol, max_iter, o, workspace_dev, y_dev, info, as_stream(stream)));
+  return done(run_cg_batched(n, lats, x, b, y, mass, tol, max_iter, o, workspace_dev, info, as_stream(stream)));
 }
 
 }  // extern "C"

@@ -1,0 +1,426 @@
+// Conjugate-gradient building blocks shared by the single-RHS, multi-RHS and batched solvers:
+// device scalars, the fused epilogues, the reliable-update and output kernels, the workspace
+// layout and the single-RHS launch sequences.
+#pragma once
+
+#include <type_traits>
+
+#include "dslash.cuh"
+
+
+namespace qcd {
+
+struct __align__(256) CgScalars {
+  double rr, rr_prev, pp, alpha, beta, delit, bb, m2, res2, rmax2, delta2, tol2;
+  int iter, max_iter, done, since_ru, ru_count, ru_interval, mixed, pad;
+  unsigned counter[16];
+};
+static_assert(sizeof(CgScalars) <= 256, "scalars block");
+
+// kConverged: the recursion met tol (final for plain FP64; the mixed solver confirms it with a
+// reliable update, which ends in kTrueConverged or back in kRunning).
+enum { kRunning = 0, kConverged = 1, kMaxIter = 2, kBreakdown = 3, kReliable = 4, kTrueConverged = 5 };
+
+__device__ __forceinline__ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+// ---------------------------------------------------------------- init: r = b_e, x = 0, p = 0
+template <class FieldT, class XFieldT>
+__global__ void __launch_bounds__(kBlock) cg_init_kernel(Geom g, const double2* __restrict__ b_canon,
+                                                         Field<QCD_PREC_DOUBLE> b_hi, Field<QCD_PREC_DOUBLE> x_hi,
+                                                         FieldT r, FieldT p, XFieldT x_lo, int mixed, CgScalars* sc,
+                                                         double* partials) {
+  using T = typename FieldT::T;
+  using TX = typename XFieldT::T;
+  double red[1] = {0.0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
+    const Site s = site_of(g, k, QCD_EVEN);
+    cvec3<double> b;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double2 d = b_canon[(size_t)s.lex * 3 + a];
+      b.c[a].re = d.x; b.c[a].im = d.y;
+    }
+    b_hi.store(k, b);
+    cvec3<T> bl, z;
+    zero(z);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { bl.c[a].re = (T)b.c[a].re; bl.c[a].im = (T)b.c[a].im; }
+    r.store(k, bl);
+    p.store(k, z);
+    cvec3<TX> zx;
+    zero(zx);
+    x_lo.store(k, zx);
+    if (mixed) {
+      cvec3<double> zd;
+      zero(zd);
+      x_hi.store(k, zd);
+    }
+    red[0] += norm2(b);
+  }
+  double tot[1];
+  if (grid_sum_last_block<1>(red, partials, &sc->counter[0], tot) && threadIdx.x == 0) {
+    const double bb = tot[0];
+    sc->bb = bb;
+    sc->rr = bb;
+    sc->rr_prev = bb;
+    sc->rmax2 = bb;
+    sc->pp = 0.0;
+    sc->beta = 0.0;
+    sc->alpha = 0.0;
+    sc->delit = sc->tol2 * bb;
+    sc->iter = 0;
+    sc->since_ru = 0;
+    sc->ru_count = 0;
+    sc->done = !isfinite(bb) ? kBreakdown : (bb == 0.0 ? kTrueConverged : kRunning);
+  }
+}
+
+// ---------------------------------------------------------------- K3: p = r + beta p
+template <class FieldT>
+__global__ void __launch_bounds__(kBlock) cg_p_kernel(int Vh, FieldT r, FieldT p, CgScalars* sc, double* partials) {
+  using T = typename FieldT::T;
+  if (sc->done != kRunning) return;
+  const T beta = (T)sc->beta;
+  double red[1] = {0.0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Vh; k += gridDim.x * blockDim.x) {
+    cvec3<T> rv = r.load(k), pv = p.load(k);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      pv.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
+      pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
+    }
+    p.store(k, pv);
+    red[0] += (double)norm2(pv);
+  }
+  double tot[1];
+  if (grid_sum_last_block<1>(red, partials, &sc->counter[1], tot) && threadIdx.x == 0) sc->pp = tot[0];
+}
+
+// ---------------------------------------------------------------- K1 epilogue: ap = D_oe p
+template <class FieldT>
+struct EpiAp {
+  static constexpr int NV = 1;
+  FieldT ap;
+  CgScalars* sc;
+  double* partials;
+  __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
+  template <class T>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double* red) const {
+    ap.store(k, acc);
+    red[0] += (double)norm2(acc);
+  }
+  __device__ __forceinline__ void finish(double* red) const {
+    double v[1] = {red[0]}, tot[1];
+    if (grid_sum_last_block<1>(v, partials, &sc->counter[2], tot) && threadIdx.x == 0) {
+      const double d = tot[0] + sc->m2 * sc->pp;  // <p, A p> = |D_oe p|^2 + m^2 |p|^2
+      const double alpha = sc->rr / d;
+      if (!finite_pos(d) || !isfinite(alpha)) {
+        sc->done = kBreakdown;
+      } else {
+        sc->alpha = alpha;
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------- K2 epilogue: update x, r
+template <class FieldT, class XFieldT>
+struct EpiUpdate {
+  static constexpr int NV = 1;
+  FieldT p, r;
+  XFieldT x;
+  CgScalars* sc;
+  double* partials;
+  __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
+  template <class T>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double* red) const {
+    using TX = typename XFieldT::T;
+    const T alpha = (T)sc->alpha, m2 = (T)sc->m2;
+    const cvec3<T> pv = p.load(k);
+    cvec3<T> rv = r.load(k);
+    cvec3<TX> xv = x.load(k);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T at_re = fma(m2, pv.c[a].re, -acc.c[a].re);  // (A p)_a = m^2 p - D_eo D_oe p
+      const T at_im = fma(m2, pv.c[a].im, -acc.c[a].im);
+      rv.c[a].re = fma(-alpha, at_re, rv.c[a].re);
+      rv.c[a].im = fma(-alpha, at_im, rv.c[a].im);
+      xv.c[a].re = fma((TX)alpha, (TX)pv.c[a].re, xv.c[a].re);
+      xv.c[a].im = fma((TX)alpha, (TX)pv.c[a].im, xv.c[a].im);
+    }
+    r.store(k, rv);
+    x.store(k, xv);
+    red[0] += (double)norm2(rv);
+  }
+  __device__ __forceinline__ void finish(double* red) const {
+    double v[1] = {red[0]}, tot[1];
+    if (grid_sum_last_block<1>(v, partials, &sc->counter[3], tot) && threadIdx.x == 0) {
+      const double rr = tot[0];
+      sc->iter += 1;
+      sc->since_ru += 1;
+      sc->rr_prev = sc->rr;
+      sc->rr = rr;
+      if (!isfinite(rr)) {
+        sc->done = kBreakdown;
+        return;
+      }
+      sc->beta = rr / sc->rr_prev;
+      if (rr > sc->rmax2) sc->rmax2 = rr;
+      if (rr < sc->delit) {
+        sc->done = kConverged;  // mixed: confirmed by a reliable update on the host's next check
+      } else if (sc->iter >= sc->max_iter) {
+        sc->done = kMaxIter;
+      } else if (sc->mixed && (sc->since_ru >= sc->ru_interval || rr < sc->delta2 * sc->rmax2)) {
+        sc->done = kReliable;
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------- reliable update (FP64)
+// x_hi += x_lo, x_lo = 0
+template <class XFieldT>
+__global__ void __launch_bounds__(kBlock) ru_accumulate_kernel(int Vh, Field<QCD_PREC_DOUBLE> x_hi, XFieldT x_lo) {
+  using TX = typename XFieldT::T;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Vh; k += gridDim.x * blockDim.x) {
+    cvec3<double> xh = x_hi.load(k);
+    const cvec3<TX> xl = x_lo.load(k);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { xh.c[a].re += (double)xl.c[a].re; xh.c[a].im += (double)xl.c[a].im; }
+    x_hi.store(k, xh);
+    cvec3<TX> z;
+    zero(z);
+    x_lo.store(k, z);
+  }
+}
+
+// r_hi = b - (m^2 x_hi - D_eo tmp) with tmp = D_oe x_hi; the low-precision r takes r_hi.
+template <class FieldT>
+struct EpiReliable {
+  static constexpr int NV = 1;
+  Field<QCD_PREC_DOUBLE> b, x;
+  FieldT r_lo;
+  CgScalars* sc;
+  double* partials;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void site(int k, cvec3<double>& acc, double* red) const {
+    using T = typename FieldT::T;
+    const cvec3<double> bv = b.load(k), xv = x.load(k);
+    cvec3<double> rv;
+    cvec3<T> rl;
+    const double m2 = sc->m2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      rv.c[a].re = bv.c[a].re - fma(m2, xv.c[a].re, -acc.c[a].re);
+      rv.c[a].im = bv.c[a].im - fma(m2, xv.c[a].im, -acc.c[a].im);
+      rl.c[a].re = (T)rv.c[a].re;
+      rl.c[a].im = (T)rv.c[a].im;
+    }
+    r_lo.store(k, rl);
+    red[0] += norm2(rv);
+  }
+  __device__ __forceinline__ void finish(double* red) const {
+    double v[1] = {red[0]}, tot[1];
+    if (grid_sum_last_block<1>(v, partials, &sc->counter[4], tot) && threadIdx.x == 0) {
+      const double rr = tot[0];
+      if (!isfinite(rr)) {
+        sc->done = kBreakdown;
+        return;
+      }
+      sc->beta = sc->iter > 0 ? rr / sc->rr_prev : 0.0;
+      sc->rr = rr;
+      sc->rmax2 = rr;
+      sc->since_ru = 0;
+      sc->ru_count += 1;
+      sc->res2 = rr;
+      if (rr < sc->delit) sc->done = kTrueConverged;
+      else if (sc->iter >= sc->max_iter) sc->done = kMaxIter;
+      else sc->done = kRunning;
+    }
+  }
+};
+
+// Final true residual: res = b - (m^2 x - D_eo y), y = D_oe x.
+struct EpiResidual {
+  static constexpr int NV = 1;
+  Field<QCD_PREC_DOUBLE> b, x;
+  CgScalars* sc;
+  double* partials;
+  __device__ __forceinline__ bool skip() const { return false; }
+  __device__ __forceinline__ void site(int k, cvec3<double>& acc, double* red) const {
+    const cvec3<double> bv = b.load(k), xv = x.load(k);
+    const double m2 = sc->m2;
+    cvec3<double> rv;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      rv.c[a].re = bv.c[a].re - fma(m2, xv.c[a].re, -acc.c[a].re);
+      rv.c[a].im = bv.c[a].im - fma(m2, xv.c[a].im, -acc.c[a].im);
+    }
+    red[0] += norm2(rv);
+  }
+  __device__ __forceinline__ void finish(double* red) const {
+    double v[1] = {red[0]}, tot[1];
+    if (grid_sum_last_block<1>(v, partials, &sc->counter[5], tot) && threadIdx.x == 0) sc->res2 = tot[0];
+  }
+};
+
+// Write x (even sites) and y (odd sites) into canonical fields, zeroing the other halves.
+static __global__ void __launch_bounds__(kBlock) cg_output_kernel(Geom g, double2* __restrict__ x_canon,
+                                                           double2* __restrict__ y_canon, Field<QCD_PREC_DOUBLE> x_e,
+                                                           Field<QCD_PREC_DOUBLE> y_o) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
+    const Site se = site_of(g, k, QCD_EVEN), so = site_of(g, k, QCD_ODD);
+    const cvec3<double> xv = x_e.load(k);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      x_canon[(size_t)se.lex * 3 + a] = make_double2(xv.c[a].re, xv.c[a].im);
+      x_canon[(size_t)so.lex * 3 + a] = make_double2(0.0, 0.0);
+    }
+    if (y_canon) {
+      const cvec3<double> yv = y_o.load(k);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        y_canon[(size_t)so.lex * 3 + a] = make_double2(yv.c[a].re, yv.c[a].im);
+        y_canon[(size_t)se.lex * 3 + a] = make_double2(0.0, 0.0);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- workspace layout
+// R right-hand sides: every field kind is R packed fields back to back, R scalar blocks.
+struct CgWork {
+  CgScalars* sc;
+  double* partials;
+  void* b_hi;
+  void* x_hi;
+  void* tmp_o;  // FP64 odd: reliable-update D_oe x and the final y
+  void* r;
+  void* p;
+  void* ap;
+  void* x_lo;
+  size_t total;
+  int R;
+  size_t f64, fin, fx;  // bytes of one field: FP64, inner precision, x accumulator
+};
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+inline CgWork carve(const qcd_lattice* lat, int prec_inner, int R, char* base) {
+  CgWork w{};
+  size_t off = 0;
+  auto take = [&](size_t n) { void* p = base ? base + off : nullptr; off += align256(n); return p; };
+  w.R = R;
+  w.sc = (CgScalars*)take(sizeof(CgScalars) * R);
+  w.partials = (double*)take(sizeof(double) * kMaxPartials * (R > 2 ? R : 2));
+  const long long Vh = lat->Vh;
+  w.f64 = field_bytes(QCD_PREC_DOUBLE, Vh);
+  w.fin = field_bytes(prec_inner, Vh);
+  w.fx = prec_inner == QCD_PREC_DOUBLE ? w.f64 : field_bytes(QCD_PREC_SINGLE, Vh);
+  w.b_hi = take(w.f64 * R);
+  w.x_hi = take(w.f64 * R);
+  w.tmp_o = take(w.f64 * R);
+  w.r = take(w.fin * R);
+  w.p = take(w.fin * R);
+  w.ap = take(w.fin * R);
+  // plain FP64: x accumulates directly in the FP64 field
+  w.x_lo = prec_inner == QCD_PREC_DOUBLE ? w.x_hi : take(w.fx * R);
+  w.total = off;
+  return w;
+}
+
+// The single-RHS view of right-hand side r.
+inline CgWork view(const CgWork& w, int r) {
+  CgWork v = w;
+  auto at = [&](void* p, size_t stride) { return p ? (void*)((char*)p + stride * r) : nullptr; };
+  v.sc = w.sc + r;
+  v.b_hi = at(w.b_hi, w.f64);
+  v.x_hi = at(w.x_hi, w.f64);
+  v.tmp_o = at(w.tmp_o, w.f64);
+  v.r = at(w.r, w.fin);
+  v.p = at(w.p, w.fin);
+  v.ap = at(w.ap, w.fin);
+  v.x_lo = at(w.x_lo, w.fx);
+  v.R = 1;
+  return v;
+}
+
+// ---------------------------------------------------------------- single-RHS launch sequences
+template <int PREC, int RECON>
+struct CgRunner {
+  using FieldT = Field<PREC>;
+  using XPREC = std::integral_constant<int, PREC == QCD_PREC_DOUBLE ? QCD_PREC_DOUBLE : QCD_PREC_SINGLE>;
+  using XFieldT = Field<XPREC::value>;
+  const qcd_lattice* lat;
+  Geom g;
+  CgWork w;
+  cudaStream_t st;
+  int grid;
+  long long launches = 0;
+
+  // One CG iteration (K3, K1, K2). With `ev` (4 events) the two operator launches are bracketed.
+  int iteration(cudaEvent_t* ev = nullptr) {
+    auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
+    FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh), ap = make_field<PREC>(w.ap, g.Vh);
+    XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
+    cg_p_kernel<<<grid, kBlock, 0, st>>>(g.Vh, r, p, w.sc, w.partials);
+    if (ev) QCD_CUDA(cudaEventRecord(ev[0], st));
+    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U, p, QCD_ODD, EpiAp<FieldT>{ap, w.sc, w.partials});
+    if (ev) QCD_CUDA(cudaEventRecord(ev[1], st));
+    if (ev) QCD_CUDA(cudaEventRecord(ev[2], st));
+    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U, ap, QCD_EVEN,
+                                           EpiUpdate<FieldT, XFieldT>{p, r, x, w.sc, w.partials});
+    if (ev) QCD_CUDA(cudaEventRecord(ev[3], st));
+    QCD_CUDA(cudaGetLastError());
+    launches += 3;
+    return QCD_OK;
+  }
+
+  int init(const void* b_canon) {
+    FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh);
+    XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
+    launches += 1;
+    cg_init_kernel<<<grid, kBlock, 0, st>>>(g, (const double2*)b_canon, make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh),
+                                            make_field<QCD_PREC_DOUBLE>(w.x_hi, g.Vh), r, p, x,
+                                            PREC != QCD_PREC_DOUBLE, w.sc, w.partials);
+    QCD_CUDA(cudaGetLastError());
+    return QCD_OK;
+  }
+
+  int reliable_update() {
+    auto U64 = make_links<QCD_PREC_DOUBLE, 18>(lat->links[QCD_PREC_DOUBLE].ptr, g.Vh);
+    auto xh = make_field<QCD_PREC_DOUBLE>(w.x_hi, g.Vh);
+    auto tmp = make_field<QCD_PREC_DOUBLE>(w.tmp_o, g.Vh);
+    launches += 3;
+    ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh));
+    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U64, xh, QCD_ODD, EpiStore<Field<QCD_PREC_DOUBLE>>{tmp});
+    EpiReliable<FieldT> epi{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, make_field<PREC>(w.r, g.Vh), w.sc,
+                            w.partials};
+    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U64, tmp, QCD_EVEN, epi);
+    QCD_CUDA(cudaGetLastError());
+    return QCD_OK;
+  }
+
+  int finish(void* x_canon, void* y_canon) {
+    auto U64 = make_links<QCD_PREC_DOUBLE, 18>(lat->links[QCD_PREC_DOUBLE].ptr, g.Vh);
+    auto xh = make_field<QCD_PREC_DOUBLE>(w.x_hi, g.Vh);
+    auto tmp = make_field<QCD_PREC_DOUBLE>(w.tmp_o, g.Vh);
+    launches += PREC != QCD_PREC_DOUBLE ? 4 : 3;
+    if (PREC != QCD_PREC_DOUBLE)
+      ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh));
+    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U64, xh, QCD_ODD, EpiStore<Field<QCD_PREC_DOUBLE>>{tmp});
+    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U64, tmp, QCD_EVEN,
+                                           EpiResidual{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, w.sc, w.partials});
+    cg_output_kernel<<<grid, kBlock, 0, st>>>(g, (double2*)x_canon, (double2*)y_canon, xh, tmp);
+    QCD_CUDA(cudaGetLastError());
+    return QCD_OK;
+  }
+};
+
+inline int read_scalars(const CgWork& w, CgScalars* h, cudaStream_t st, int count = 1) {
+  QCD_CUDA(cudaMemcpyAsync(h, w.sc, sizeof(CgScalars) * count, cudaMemcpyDeviceToHost, st));
+  QCD_CUDA(cudaStreamSynchronize(st));
+  return QCD_OK;
+}
+
+}  // namespace qcd

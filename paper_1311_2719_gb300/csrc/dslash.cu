@@ -76,21 +76,6 @@ int launch_mdagm(const qcd_lattice* lat, void* out, const void* in, double mass,
 // Multi-RHS hop: each thread owns one output site and applies every loaded link to RB
 // right-hand sides before moving on, so a link is read once per RB vectors.
 // ------------------------------------------------------------------------------------------
-template <class FieldT>
-__device__ __forceinline__ FieldT field_at(const FieldT& f, int r) {
-  FieldT o = f;
-  o.p = f.p + (size_t)r * FieldT::kElemsPerSite * f.Vh;
-  return o;
-}
-
-template <typename T>
-__device__ __forceinline__ void scale(su3<T>& U, T s) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) { U.e[a][b].re *= s; U.e[a][b].im *= s; }
-}
-
 template <class LinksT, class FieldT, int RB>
 __global__ void __launch_bounds__(kBlock) dslash_mrhs_kernel(Geom g, LinksT U, FieldT in, FieldT out, int nrhs,
                                                              int out_par) {

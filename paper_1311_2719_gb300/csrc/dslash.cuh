@@ -70,25 +70,41 @@ struct EpiStore {
 };
 
 template <int PREC>
-inline Field<PREC> make_field(void* p, int Vh);
+__host__ __device__ inline Field<PREC> make_field(void* p, int Vh);
 template <>
-inline Field<QCD_PREC_DOUBLE> make_field<QCD_PREC_DOUBLE>(void* p, int Vh) { return {(double2*)p, Vh}; }
+__host__ __device__ inline Field<QCD_PREC_DOUBLE> make_field<QCD_PREC_DOUBLE>(void* p, int Vh) { return {(double2*)p, Vh}; }
 template <>
-inline Field<QCD_PREC_SINGLE> make_field<QCD_PREC_SINGLE>(void* p, int Vh) { return {(float2*)p, Vh}; }
+__host__ __device__ inline Field<QCD_PREC_SINGLE> make_field<QCD_PREC_SINGLE>(void* p, int Vh) { return {(float2*)p, Vh}; }
 template <>
-inline Field<QCD_PREC_HALF> make_field<QCD_PREC_HALF>(void* p, int Vh) { return {(uint4*)p, Vh}; }
+__host__ __device__ inline Field<QCD_PREC_HALF> make_field<QCD_PREC_HALF>(void* p, int Vh) { return {(uint4*)p, Vh}; }
 
 template <int PREC, int RECON>
-inline Links<PREC, RECON> make_links(const void* p, int Vh);
+__host__ __device__ inline Links<PREC, RECON> make_links(const void* p, int Vh);
 template <>
-inline Links<QCD_PREC_DOUBLE, 18> make_links<QCD_PREC_DOUBLE, 18>(const void* p, int Vh) { return {(const double2*)p, Vh}; }
+__host__ __device__ inline Links<QCD_PREC_DOUBLE, 18> make_links<QCD_PREC_DOUBLE, 18>(const void* p, int Vh) { return {(const double2*)p, Vh}; }
 template <>
-inline Links<QCD_PREC_SINGLE, 18> make_links<QCD_PREC_SINGLE, 18>(const void* p, int Vh) { return {(const float2*)p, Vh}; }
+__host__ __device__ inline Links<QCD_PREC_SINGLE, 18> make_links<QCD_PREC_SINGLE, 18>(const void* p, int Vh) { return {(const float2*)p, Vh}; }
 template <>
-inline Links<QCD_PREC_SINGLE, 12> make_links<QCD_PREC_SINGLE, 12>(const void* p, int Vh) { return {(const float4*)p, Vh}; }
+__host__ __device__ inline Links<QCD_PREC_SINGLE, 12> make_links<QCD_PREC_SINGLE, 12>(const void* p, int Vh) { return {(const float4*)p, Vh}; }
 template <>
-inline Links<QCD_PREC_HALF, 12> make_links<QCD_PREC_HALF, 12>(const void* p, int Vh) {
+__host__ __device__ inline Links<QCD_PREC_HALF, 12> make_links<QCD_PREC_HALF, 12>(const void* p, int Vh) {
   return {(const uint4*)p, (const uint2*)((const uint4*)p + 8 * (size_t)Vh), Vh};
+}
+
+// Field r of a multi-RHS packed field (nrhs fields back to back).
+template <class FieldT>
+__device__ __forceinline__ FieldT field_at(const FieldT& f, int r) {
+  FieldT o = f;
+  o.p = f.p + (size_t)r * FieldT::kElemsPerSite * f.Vh;
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void scale(su3<T>& U, T s) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) { U.e[a][b].re *= s; U.e[a][b].im *= s; }
 }
 
 // Grid size for the site kernels: enough blocks to cover V/2 sites, capped so that the

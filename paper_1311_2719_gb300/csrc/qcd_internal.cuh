@@ -254,6 +254,15 @@ struct Field<QCD_PREC_DOUBLE> {
     }
     return v;
   }
+  __device__ __forceinline__ cvec3<double> load_cg(int k) const {
+    cvec3<double> v;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double2 d = __ldcg(p + (size_t)a * Vh + k);
+      v.c[a].re = d.x; v.c[a].im = d.y;
+    }
+    return v;
+  }
   __device__ __forceinline__ void store(int k, const cvec3<double>& v) const {
 #pragma unroll
     for (int a = 0; a < 3; ++a) p[(size_t)a * Vh + k] = make_double2(v.c[a].re, v.c[a].im);
@@ -276,6 +285,15 @@ struct Field<QCD_PREC_SINGLE> {
     }
     return v;
   }
+  __device__ __forceinline__ cvec3<float> load_cg(int k) const {
+    cvec3<float> v;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 d = __ldcg(p + (size_t)a * Vh + k);
+      v.c[a].re = d.x; v.c[a].im = d.y;
+    }
+    return v;
+  }
   __device__ __forceinline__ void store(int k, const cvec3<float>& v) const {
 #pragma unroll
     for (int a = 0; a < 3; ++a) p[(size_t)a * Vh + k] = make_float2(v.c[a].re, v.c[a].im);
@@ -290,8 +308,9 @@ struct Field<QCD_PREC_HALF> {
   static constexpr int kElemsPerSite = 1;
   uint4* p;  // [Vh]
   int Vh;
-  __device__ __forceinline__ cvec3<float> load(int k) const {
-    uint4 q = __ldg(p + k);
+  __device__ __forceinline__ cvec3<float> load(int k) const { return decode(__ldg(p + k)); }
+  __device__ __forceinline__ cvec3<float> load_cg(int k) const { return decode(__ldcg(p + k)); }
+  __device__ __forceinline__ static cvec3<float> decode(uint4 q) {
     const float s = __uint_as_float(q.w);
     cvec3<float> v;
     const unsigned w[3] = {q.x, q.y, q.z};
@@ -323,6 +342,17 @@ inline size_t field_bytes(int prec, long long Vh) {
   }
   return 0;
 }
+
+// A field whose loads go to L2 (coherent), for data that other blocks write during the same
+// launch; the default loads use the read-only path, valid only for data fixed during a launch.
+template <class FieldT>
+struct Coherent {
+  using T = typename FieldT::T;
+  static constexpr int kElemsPerSite = FieldT::kElemsPerSite;
+  FieldT f;
+  __device__ __forceinline__ cvec3<T> load(int k) const { return f.load_cg(k); }
+  __device__ __forceinline__ void store(int k, const cvec3<T>& v) const { f.store(k, v); }
+};
 
 // ------------------------------------------------------------------------------------------
 // Packed links. Array of (parity, mu) blocks of V/2 sites each; link (par, mu, k) is U_mu at

@@ -46,6 +46,9 @@ class qcd_solver_opts(ctypes.Structure):
         ("check_interval", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("rhs_block", ctypes.c_int),
+        ("cluster_size", ctypes.c_int),
+        ("block_size", ctypes.c_int),
     ]
 
 
@@ -94,6 +97,18 @@ SIGNATURES = {
     "qcd_mdagm_noalloc": (_i, [_vp, _vp, _vp, _d, _i, _vp]),
     "qcd_cg_solve": (_i, [_vp, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp, _vp,
                           ctypes.POINTER(qcd_solve_info), _vp]),
+    "qcd_workspace_bytes_batched": (_sz, [_i, ctypes.POINTER(_vp), ctypes.POINTER(qcd_solver_opts)]),
+    "qcd_cg_solve_batched": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                  ctypes.POINTER(_vp), ctypes.POINTER(_d), _d, _i, ctypes.POINTER(qcd_solver_opts),
+                                  _vp, ctypes.POINTER(qcd_solve_info), _vp]),
+    "qcd_tune_mrhs": (_i, [_vp, _i, _vp, _vp, _d, ctypes.POINTER(qcd_solver_opts), _vp, ctypes.c_char_p,
+                           ctypes.POINTER(_i), _vp]),
+    "qcd_tune_batched": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
+                              _d, _i, ctypes.POINTER(qcd_solver_opts), _vp, ctypes.c_char_p, ctypes.POINTER(_i),
+                              ctypes.POINTER(_i), _vp]),
+    "qcd_tune_load": (_i, [ctypes.c_char_p]),
+    "qcd_cg_solve_mrhs": (_i, [_vp, _i, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp, _vp,
+                               ctypes.POINTER(qcd_solve_info), _vp]),
 }
 
 
@@ -230,6 +245,65 @@ def qcd_cg_solve(lat, x_dev, b_dev, mass, tol, max_iter, opts, workspace_dev, y_
     return rc, info.as_dict()
 
 
+def qcd_cg_solve_mrhs(lat, nrhs, x_dev, b_dev, mass, tol, max_iter, opts, workspace_dev, y_dev=None, stream=None,
+                      raise_on=(QCD_ERR_INVALID_ARG, QCD_ERR_CUDA, QCD_ERR_UNSUPPORTED, QCD_ERR_NO_LINKS)):
+    """Returns (status, [info dict per RHS])."""
+    infos = (qcd_solve_info * max(int(nrhs), 1))()
+    rc = _lib.qcd_cg_solve_mrhs(lat, int(nrhs), _ptr(x_dev), _ptr(b_dev), float(mass), float(tol), int(max_iter),
+                                ctypes.byref(opts) if opts is not None else None, _ptr(workspace_dev), _ptr(y_dev),
+                                infos, _stream(stream))
+    if rc in raise_on:
+        _check(rc, "qcd_cg_solve_mrhs")
+    return rc, [i.as_dict() for i in infos]
+
+
+def _ptr_array(items):
+    return (_vp * len(items))(*[_ptr(t) for t in items])
+
+
+def qcd_workspace_bytes_batched(lats, opts=None) -> int:
+    return _lib.qcd_workspace_bytes_batched(len(lats), _ptr_array(lats), ctypes.byref(opts) if opts is not None else None)
+
+
+def qcd_cg_solve_batched(lats, x_devs, b_devs, y_devs, masses, tol, max_iter, opts, workspace_dev, stream=None,
+                         raise_on=(QCD_ERR_INVALID_ARG, QCD_ERR_CUDA, QCD_ERR_UNSUPPORTED, QCD_ERR_NO_LINKS)):
+    """Returns (status, [info dict per lattice])."""
+    n = len(lats)
+    infos = (qcd_solve_info * max(n, 1))()
+    ys = _ptr_array(y_devs) if y_devs is not None else None
+    m = (_d * n)(*[float(v) for v in masses])
+    rc = _lib.qcd_cg_solve_batched(n, _ptr_array(lats), _ptr_array(x_devs), _ptr_array(b_devs), ys, m, float(tol),
+                                   int(max_iter), ctypes.byref(opts) if opts is not None else None,
+                                   _ptr(workspace_dev), infos, _stream(stream))
+    if rc in raise_on:
+        _check(rc, "qcd_cg_solve_batched")
+    return rc, [infos[i].as_dict() for i in range(n)]
+
+
+def qcd_tune_mrhs(lat, nrhs, x_dev, b_dev, mass, opts, workspace_dev, cache_path=None, stream=None) -> int:
+    best = _i()
+    _check(_lib.qcd_tune_mrhs(lat, int(nrhs), _ptr(x_dev), _ptr(b_dev), float(mass),
+                              ctypes.byref(opts) if opts is not None else None, _ptr(workspace_dev),
+                              cache_path.encode() if cache_path else None, ctypes.byref(best), _stream(stream)),
+           "qcd_tune_mrhs")
+    return best.value
+
+
+def qcd_tune_batched(lats, x_devs, b_devs, masses, tol, max_iter, opts, workspace_dev, cache_path=None, stream=None):
+    n = len(lats)
+    c, blk = _i(), _i()
+    m = (_d * n)(*[float(v) for v in masses])
+    _check(_lib.qcd_tune_batched(n, _ptr_array(lats), _ptr_array(x_devs), _ptr_array(b_devs), m, float(tol),
+                                 int(max_iter), ctypes.byref(opts) if opts is not None else None, _ptr(workspace_dev),
+                                 cache_path.encode() if cache_path else None, ctypes.byref(c), ctypes.byref(blk),
+                                 _stream(stream)), "qcd_tune_batched")
+    return c.value, blk.value
+
+
+def qcd_tune_load(cache_path: str) -> None:
+    _check(_lib.qcd_tune_load(cache_path.encode()), "qcd_tune_load")
+
+
 # ---------------------------------------------------------------- convenience owner object
 
 class Lattice:
@@ -266,9 +340,9 @@ class Lattice:
         self._links[prec] = buf
         return buf
 
-    def workspace(self, opts: qcd_solver_opts):
-        n = qcd_workspace_bytes(self.handle, opts, 1)
-        key = (opts.prec_inner,)
+    def workspace(self, opts: qcd_solver_opts, nrhs: int = 1):
+        n = qcd_workspace_bytes(self.handle, opts, nrhs)
+        key = (opts.prec_inner, nrhs)
         if key not in self._ws or self._ws[key].numel() < n:
             self._ws[key] = self.empty_bytes(n)
         return self._ws[key]
