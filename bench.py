@@ -46,6 +46,11 @@ WORKLOADS = {
                           desc="staggered 32^4 Haar, m=0.01, mixed CG: FP32 recon-12 inner, FP64 reliable updates"),
     "cg32_half12": dict(dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="half12",
                         desc="staggered 32^4 Haar, m=0.01, mixed CG: FP16+scale recon-12 inner, FP64 reliable updates"),
+    "cg16_df64": dict(dims=(16, 16, 16, 16), kind="haar", mass=0.1, tol=1e-10, inner="df64",
+                      desc="staggered 16^4 Haar SU(3), m=0.1, even-odd CG in df64 (float-float on the FP32 pipes) "
+                           "with FP64 reliable updates, to true rel. residual 1e-10"),
+    "cg32_df64": dict(dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="df64",
+                      desc="staggered 32^4 Haar, m=0.01, even-odd CG in df64 with FP64 reliable updates"),
     "mrhs24_single12": dict(kind_solve="mrhs", dims=(24, 24, 24, 24), kind="haar", mass=0.05, tol=1e-10,
                             inner="single12", nrhs=16,
                             desc="staggered 24^4 Haar, m=0.05, 16 RHS in one multi-RHS CG: FP32 recon-12 inner, "
@@ -55,9 +60,10 @@ WORKLOADS = {
                                   "persistent clustered CG launch: FP32 recon-12 inner, FP64 reliable updates"),
 }
 DEFAULT_WORKLOAD = "cg16_fp64"
-PRECS = {"double": (0, 18), "single18": (1, 18), "single12": (1, 12), "half12": (2, 12)}
+PRECS = {"double": (0, 18), "single18": (1, 18), "single12": (1, 12), "half12": (2, 12), "df64": (3, 18)}
 DTYPE = {"double": "f64", "single18": "f32 (FP64 reliable updates)", "single12": "f32 (FP64 reliable updates)",
-         "half12": "f16-storage/f32 (FP64 reliable updates)"}
+         "half12": "f16-storage/f32 (FP64 reliable updates)",
+         "df64": "df64 (float-float, 48-bit significand; FP64 reliable updates)"}
 
 
 def _env_rank():
@@ -227,15 +233,14 @@ def run_gpu(args, wl):
     d_n = sum(i["dslash_launches"] for i in infos_prof)
     per_launch_ms = d_ms / d_n
     achieved_tflops = FLOP_PER_SITE * Vh / (per_launch_ms * 1e-3) / 1e12
-    if inner == "double":
-        link_b, vec_b = 1152, 96
-    elif inner == "single18":
-        link_b, vec_b = 576, 48
-    elif inner == "single12":
-        link_b, vec_b = 384, 48
-    else:
-        link_b, vec_b = 192, 32
-    alg_bytes = (link_b + vec_b) * Vh
+    # algorithmic bytes per site of the two operator launches of an iteration (links and every
+    # vector read or written once): K1 = links + p (in) + ap (out); K2 = links + ap (in) + p, r, x
+    # read + r, x written. The average of the two is the per-launch figure.
+    link_b, fld_b, x_b = {"double": (1152, 48, 48), "single18": (576, 24, 24), "single12": (384, 24, 24),
+                          "half12": (192, 16, 24), "df64": (1152, 48, 48)}[inner]
+    k1_b = link_b + 2 * fld_b
+    k2_b = link_b + fld_b + 2 * fld_b + x_b + fld_b + x_b
+    alg_bytes = (k1_b + k2_b) / 2 * Vh
     achieved_gbs = alg_bytes / (per_launch_ms * 1e-3) / 1e9
     peaks = {}
     try:
@@ -250,13 +255,14 @@ def run_gpu(args, wl):
                     "peak_source": "derived FP64 FMA peak (152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz)",
                     "traffic": None,
                     "hbm_model_gbs": round(achieved_gbs, 1), "hbm_model_frac": round(achieved_gbs / hbm_peak, 4),
-                    "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": FLOP_PER_SITE * Vh,
-                    "avg_launch_us": round(per_launch_ms * 1e3, 3)}
+                    "alg_bytes_per_launch": alg_bytes, "alg_bytes_per_site_k1_k2": [k1_b, k2_b],
+                    "alg_flops_per_launch": FLOP_PER_SITE * Vh, "avg_launch_us": round(per_launch_ms * 1e3, 3)}
     else:
         roofline = {"bound": "hbm", "kernel": "dslash_kernel (CG K1+K2 launches)", "achieved": round(achieved_gbs, 1),
                     "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 4),
                     "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
-                    "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": FLOP_PER_SITE * Vh,
+                    "alg_bytes_per_launch": alg_bytes, "alg_bytes_per_site_k1_k2": [k1_b, k2_b],
+                    "alg_flops_per_launch": FLOP_PER_SITE * Vh,
                     "achieved_tflops": round(achieved_tflops, 4), "avg_launch_us": round(per_launch_ms * 1e3, 3)}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,

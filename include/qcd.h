@@ -20,7 +20,8 @@
  *                         (V/2 sites) at one precision; size from qcd_field_bytes().
  *                         Site k of parity p is the canonical site i with i >> 1 == k.
  *                         QCD_PREC_DOUBLE: double2[3][V/2]; QCD_PREC_SINGLE: float2[3][V/2];
- *                         QCD_PREC_HALF: 16 bytes per site {3 x half2 colour, float scale}.
+ *                         QCD_PREC_HALF: 16 bytes per site {3 x half2 colour, float scale};
+ *                         QCD_PREC_DF64: float4[3][V/2] {re.hi, re.lo, im.hi, im.lo}.
  *   A multi-RHS packed field is nrhs packed fields back to back.
  *
  * Memory ownership
@@ -61,14 +62,18 @@ typedef enum {
 } qcd_status;
 
 enum { QCD_EVEN = 0, QCD_ODD = 1 };
-enum { QCD_PREC_DOUBLE = 0, QCD_PREC_SINGLE = 1, QCD_PREC_HALF = 2 };
+/* QCD_PREC_DF64: every real held as an unevaluated sum of two FP32 values (48-bit significand),
+ * stored in the same 16 bytes per complex number as FP64 and computed on the FP32 pipes; relative
+ * error ~1e-14 against FP64 (links: reconstruct-18 only). */
+enum { QCD_PREC_DOUBLE = 0, QCD_PREC_SINGLE = 1, QCD_PREC_HALF = 2, QCD_PREC_DF64 = 3 };
 enum { QCD_RECON_18 = 18, QCD_RECON_12 = 12 };
 
 typedef struct qcd_lattice qcd_lattice; /* opaque host-side handle */
 
 /* Solver options (qcd_solver_opts_default fills the defaults noted here). */
 typedef struct {
-  int prec_inner;        /* QCD_PREC_DOUBLE (plain FP64 CG, default), _SINGLE or _HALF (mixed) */
+  int prec_inner;        /* QCD_PREC_DOUBLE (plain FP64 CG, default); _SINGLE, _HALF or _DF64 run the
+                            recursion in that precision with FP64 reliable updates                */
   int recon_inner;       /* link compression for the inner operator: 18 (default) or 12          */
   double reliable_delta; /* mixed CG: reliable update when |r| < delta * max|r| since the last (0.1) */
   int reliable_interval; /* mixed CG: and at least every this many iterations (100)              */
@@ -123,7 +128,7 @@ QCD_API int qcd_lattice_device(const qcd_lattice* lat);
 /* Bytes of one packed single-parity field at `prec` (0 on a bad argument). */
 QCD_API size_t qcd_field_bytes(const qcd_lattice* lat, int prec);
 /* Bytes of the packed gauge field at (prec, recon). Supported: DOUBLE/18, SINGLE/18, SINGLE/12,
- * HALF/12. 0 on an unsupported pair. */
+ * HALF/12, DF64/18. 0 on an unsupported pair. */
 QCD_API size_t qcd_links_bytes(const qcd_lattice* lat, int prec, int recon);
 /* Bytes of the device workspace qcd_cg_solve (nrhs = 1) or qcd_cg_solve_mrhs (1 <= nrhs <= 16)
  * needs for these options; 0 on a bad argument. */

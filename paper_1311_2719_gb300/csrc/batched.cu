@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
                                                                     unsigned* queue, int ru_interval, double delta2) {
   using FieldT = Field<PREC>;
   using T = typename FieldT::T;
-  constexpr int XP = PREC == QCD_PREC_DOUBLE ? QCD_PREC_DOUBLE : QCD_PREC_SINGLE;
+  constexpr int XP = x_prec(PREC);
   using XFieldT = Field<XP>;
   using TX = typename XFieldT::T;
   constexpr bool mixed = PREC != QCD_PREC_DOUBLE;
@@ -208,22 +208,20 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
       beta = rr / rr_prev;
       rmax2 = fmax(rmax2, rr);
       const bool met = rr < delit;
-      if (!mixed) {
-        if (met) break;
-        if (iter >= I.max_iter) { status = kBatchMaxIter; break; }
-        continue;
-      }
-      if (met || since_ru >= ru_interval || rr < delta2 * rmax2) {
-        // reliable update: x_hi += x_lo, x_lo = 0; r = b - A x_hi in FP64; r_lo <- r
-        for (int k = tid; k < Vh; k += nthreads) {
-          cvec3<double> xh = x_hi.load(k);
-          const cvec3<TX> xl = x.load(k);
+      // reliable update (mixed: periodic / delta test; both: to confirm convergence on the true
+      // residual): x_hi += x_lo, x_lo = 0; r = b - A x_hi in FP64; r_lo <- r
+      if (met || (mixed && (since_ru >= ru_interval || rr < delta2 * rmax2))) {
+        if (mixed) {
+          for (int k = tid; k < Vh; k += nthreads) {
+            cvec3<double> xh = x_hi.load(k);
+            const cvec3<TX> xl = x.load(k);
 #pragma unroll
-          for (int a = 0; a < 3; ++a) { xh.c[a].re += (double)xl.c[a].re; xh.c[a].im += (double)xl.c[a].im; }
-          x_hi.store(k, xh);
-          cvec3<TX> zx;
-          zero(zx);
-          x.store(k, zx);
+            for (int a = 0; a < 3; ++a) { xh.c[a].re += (double)xl.c[a].re; xh.c[a].im += (double)xl.c[a].im; }
+            x_hi.store(k, xh);
+            cvec3<TX> zx;
+            zero(zx);
+            x.store(k, zx);
+          }
         }
         cluster_barrier(cluster);
         for (int k = tid; k < Vh; k += nthreads) tmp.store(k, hop(g, U64, x_hi, QCD_ODD, k));
@@ -325,7 +323,7 @@ static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 static size_t lattice_fields_bytes(const qcd_lattice* lat, int prec) {
   const size_t f64 = a256(field_bytes(QCD_PREC_DOUBLE, lat->Vh));
   const size_t fin = a256(field_bytes(prec, lat->Vh));
-  const size_t fx = prec == QCD_PREC_DOUBLE ? 0 : a256(field_bytes(QCD_PREC_SINGLE, lat->Vh));
+  const size_t fx = prec == QCD_PREC_DOUBLE ? 0 : a256(field_bytes(x_prec(prec), lat->Vh));
   return 3 * f64 + 3 * fin + fx;
 }
 
@@ -477,6 +475,7 @@ int run_cg_batched(int n, qcd_lattice* const* lats, void* const* x, const void* 
   if (prec == QCD_PREC_SINGLE && recon == 18) return batched_typed<QCD_PREC_SINGLE, 18>(n, lats, x, b, y, mass, tol, max_iter, o, ws, info, st);
   if (prec == QCD_PREC_SINGLE && recon == 12) return batched_typed<QCD_PREC_SINGLE, 12>(n, lats, x, b, y, mass, tol, max_iter, o, ws, info, st);
   if (prec == QCD_PREC_HALF && recon == 12) return batched_typed<QCD_PREC_HALF, 12>(n, lats, x, b, y, mass, tol, max_iter, o, ws, info, st);
+  if (prec == QCD_PREC_DF64 && recon == 18) return batched_typed<QCD_PREC_DF64, 18>(n, lats, x, b, y, mass, tol, max_iter, o, ws, info, st);
   return QCD_ERR_UNSUPPORTED;
 }
 

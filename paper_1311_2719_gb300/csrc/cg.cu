@@ -33,7 +33,8 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
   R.g = make_geom(lat);
   R.w = carve(lat, PREC, 1, (char*)ws);
   R.st = st;
-  R.grid = site_grid(lat->Vh);
+  R.tps = threads_per_site(PREC, lat->Vh);
+  R.grid = cg_grid<PREC, RECON>(lat->Vh, R.tps);
   const bool mixed = PREC != QCD_PREC_DOUBLE;
 
   CgScalars h{};
@@ -85,8 +86,8 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
   while (true) {
     if (h.done == kBreakdown) { status = QCD_ERR_BREAKDOWN; break; }
     if (h.done == kMaxIter) { status = QCD_ERR_NOT_CONVERGED; break; }
-    if (h.done == kTrueConverged || (h.done == kConverged && !mixed)) break;
-    if (mixed && (h.done == kConverged || h.done == kReliable)) {
+    if (h.done == kTrueConverged) break;
+    if (h.done == kConverged || (mixed && h.done == kReliable)) {
       rc = R.reliable_update();
       if (rc) { cleanup(); return rc; }
       if ((rc = read_scalars(R.w, &h, st))) { cleanup(); return rc; }
@@ -152,6 +153,7 @@ int run_cg(qcd_lattice* lat, void* x, const void* b, double mass, double tol, in
   if (prec == QCD_PREC_SINGLE && recon == 18) return cg_typed<QCD_PREC_SINGLE, 18>(lat, x, b, mass, tol, max_iter, o, ws, y, info, st);
   if (prec == QCD_PREC_SINGLE && recon == 12) return cg_typed<QCD_PREC_SINGLE, 12>(lat, x, b, mass, tol, max_iter, o, ws, y, info, st);
   if (prec == QCD_PREC_HALF && recon == 12) return cg_typed<QCD_PREC_HALF, 12>(lat, x, b, mass, tol, max_iter, o, ws, y, info, st);
+  if (prec == QCD_PREC_DF64 && recon == 18) return cg_typed<QCD_PREC_DF64, 18>(lat, x, b, mass, tol, max_iter, o, ws, y, info, st);
   return QCD_ERR_UNSUPPORTED;
 }
 

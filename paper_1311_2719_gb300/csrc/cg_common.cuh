@@ -17,8 +17,8 @@ struct __align__(256) CgScalars {
 };
 static_assert(sizeof(CgScalars) <= 256, "scalars block");
 
-// kConverged: the recursion met tol (final for plain FP64; the mixed solver confirms it with a
-// reliable update, which ends in kTrueConverged or back in kRunning).
+// kConverged: the recursion met tol; the solver confirms it by replacing r with the true FP64
+// residual (a reliable update), which ends in kTrueConverged or back in kRunning.
 enum { kRunning = 0, kConverged = 1, kMaxIter = 2, kBreakdown = 3, kReliable = 4, kTrueConverged = 5 };
 
 __device__ __forceinline__ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
@@ -316,7 +316,7 @@ inline CgWork carve(const qcd_lattice* lat, int prec_inner, int R, char* base) {
   const long long Vh = lat->Vh;
   w.f64 = field_bytes(QCD_PREC_DOUBLE, Vh);
   w.fin = field_bytes(prec_inner, Vh);
-  w.fx = prec_inner == QCD_PREC_DOUBLE ? w.f64 : field_bytes(QCD_PREC_SINGLE, Vh);
+  w.fx = field_bytes(x_prec(prec_inner), Vh);
   w.b_hi = take(w.f64 * R);
   w.x_hi = take(w.f64 * R);
   w.tmp_o = take(w.f64 * R);
@@ -349,14 +349,22 @@ inline CgWork view(const CgWork& w, int r) {
 template <int PREC, int RECON>
 struct CgRunner {
   using FieldT = Field<PREC>;
-  using XPREC = std::integral_constant<int, PREC == QCD_PREC_DOUBLE ? QCD_PREC_DOUBLE : QCD_PREC_SINGLE>;
+  using XPREC = std::integral_constant<int, x_prec(PREC)>;
   using XFieldT = Field<XPREC::value>;
   const qcd_lattice* lat;
   Geom g;
   CgWork w;
   cudaStream_t st;
   int grid;
+  int tps = 1;  // threads per site of the operator kernels
   long long launches = 0;
+
+  // One operator launch with epilogue `epi` at the runner's threads-per-site.
+  template <class LinksT, class InT, class Epi>
+  void op(const LinksT& U, const InT& in, int out_par, const Epi& epi) {
+    if (tps == 2) dslash_kernel<LinksT, InT, Epi, 2><<<grid, kBlock, 0, st>>>(g, U, in, out_par, epi);
+    else dslash_kernel<LinksT, InT, Epi, 1><<<grid, kBlock, 0, st>>>(g, U, in, out_par, epi);
+  }
 
   // One CG iteration (K3, K1, K2). With `ev` (4 events) the two operator launches are bracketed.
   int iteration(cudaEvent_t* ev = nullptr) {
@@ -365,11 +373,10 @@ struct CgRunner {
     XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
     cg_p_kernel<<<grid, kBlock, 0, st>>>(g.Vh, r, p, w.sc, w.partials);
     if (ev) QCD_CUDA(cudaEventRecord(ev[0], st));
-    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U, p, QCD_ODD, EpiAp<FieldT>{ap, w.sc, w.partials});
+    op(U, p, QCD_ODD, EpiAp<FieldT>{ap, w.sc, w.partials});
     if (ev) QCD_CUDA(cudaEventRecord(ev[1], st));
     if (ev) QCD_CUDA(cudaEventRecord(ev[2], st));
-    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U, ap, QCD_EVEN,
-                                           EpiUpdate<FieldT, XFieldT>{p, r, x, w.sc, w.partials});
+    op(U, ap, QCD_EVEN, EpiUpdate<FieldT, XFieldT>{p, r, x, w.sc, w.partials});
     if (ev) QCD_CUDA(cudaEventRecord(ev[3], st));
     QCD_CUDA(cudaGetLastError());
     launches += 3;
@@ -387,16 +394,19 @@ struct CgRunner {
     return QCD_OK;
   }
 
+  // Replace the iterated residual by the true one, r = b - A x_hi in FP64 (mixed: after folding
+  // x_lo into x_hi). Plain FP64 runs it once the recursion meets tol, to confirm on the true
+  // residual; the mixed solver also every reliable_interval iterations / on the delta test.
   int reliable_update() {
     auto U64 = make_links<QCD_PREC_DOUBLE, 18>(lat->links[QCD_PREC_DOUBLE].ptr, g.Vh);
     auto xh = make_field<QCD_PREC_DOUBLE>(w.x_hi, g.Vh);
     auto tmp = make_field<QCD_PREC_DOUBLE>(w.tmp_o, g.Vh);
-    launches += 3;
-    ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh));
-    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U64, xh, QCD_ODD, EpiStore<Field<QCD_PREC_DOUBLE>>{tmp});
-    EpiReliable<FieldT> epi{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, make_field<PREC>(w.r, g.Vh), w.sc,
-                            w.partials};
-    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U64, tmp, QCD_EVEN, epi);
+    launches += PREC != QCD_PREC_DOUBLE ? 3 : 2;
+    if (PREC != QCD_PREC_DOUBLE)  // plain FP64: x_lo is x_hi itself
+      ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh));
+    op(U64, xh, QCD_ODD, EpiStore<Field<QCD_PREC_DOUBLE>>{tmp});
+    op(U64, tmp, QCD_EVEN,
+       EpiReliable<FieldT>{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, make_field<PREC>(w.r, g.Vh), w.sc, w.partials});
     QCD_CUDA(cudaGetLastError());
     return QCD_OK;
   }
@@ -408,14 +418,23 @@ struct CgRunner {
     launches += PREC != QCD_PREC_DOUBLE ? 4 : 3;
     if (PREC != QCD_PREC_DOUBLE)
       ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh));
-    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U64, xh, QCD_ODD, EpiStore<Field<QCD_PREC_DOUBLE>>{tmp});
-    dslash_kernel<<<grid, kBlock, 0, st>>>(g, U64, tmp, QCD_EVEN,
-                                           EpiResidual{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, w.sc, w.partials});
+    op(U64, xh, QCD_ODD, EpiStore<Field<QCD_PREC_DOUBLE>>{tmp});
+    op(U64, tmp, QCD_EVEN, EpiResidual{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, w.sc, w.partials});
     cg_output_kernel<<<grid, kBlock, 0, st>>>(g, (double2*)x_canon, (double2*)y_canon, xh, tmp);
     QCD_CUDA(cudaGetLastError());
     return QCD_OK;
   }
 };
+
+// One-wave grid of the CG kernels of (PREC, RECON), sized on the heaviest of them (K2). The same
+// value serves every RHS count so that multi-RHS and single-RHS reductions sum identically.
+template <int PREC, int RECON>
+inline int cg_grid(long long Vh, int tps) {
+  using FieldT = Field<PREC>;
+  using XFieldT = Field<x_prec(PREC)>;
+  if (tps == 2) return one_wave_grid(Vh, dslash_kernel<Links<PREC, RECON>, FieldT, EpiUpdate<FieldT, XFieldT>, 2>, 2);
+  return one_wave_grid(Vh, dslash_kernel<Links<PREC, RECON>, FieldT, EpiUpdate<FieldT, XFieldT>, 1>, 1);
+}
 
 inline int read_scalars(const CgWork& w, CgScalars* h, cudaStream_t st, int count = 1) {
   QCD_CUDA(cudaMemcpyAsync(h, w.sc, sizeof(CgScalars) * count, cudaMemcpyDeviceToHost, st));

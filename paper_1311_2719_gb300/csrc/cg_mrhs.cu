@@ -1,412 +1,13 @@
-// Multi-RHS even-odd CG: R independent CG recursions on one lattice that share every link load.
-//
-// The iteration is the single-RHS one (K3 p-update, K1 D_oe p, K2 D_eo ap + x/r update) with the
-// operator kernels applying each loaded link to a block of RB right-hand sides held in registers
-// (grid.y enumerates the RHS blocks; with RB = R every link is read once per half-lattice hop).
-// Each RHS keeps its own device scalars and convergence flag; converged RHS are skipped inside
-// the kernels. Reliable updates, start-up and the final y / true residual reuse the single-RHS
-// launch sequences on per-RHS views of the workspace.
-#include <chrono>
-#include <cmath>
-#include <string>
-#include <vector>
-
-#include "cg_common.cuh"
+// Multi-RHS CG entry: dispatch to the per-precision instantiations (cg_mrhs_*.cu).
+#include "cg_mrhs.cuh"
 
 namespace qcd {
 
-std::string mrhs_key(const qcd_lattice* lat, int prec, int recon, int nrhs);
-bool tune_lookup(const std::string& key, std::vector<int>* out);
-
-// Counter slots in sc[0] used by the multi-RHS kernels (single-RHS kernels use 0..5 of each sc[r]).
-enum { kCtrK3M = 8, kCtrK1M = 9, kCtrK2M = 10 };
-
-// Write this block's RB partial sums for RHS r0..r0+RB-1; true in the block that finishes last
-// over the whole (x, y) grid.
-template <int RB>
-__device__ __forceinline__ bool mrhs_arrive(double (&v)[RB], int r0, int nrhs, double* partials, unsigned* counter) {
-  __shared__ bool am_last;
-  block_sum<RB>(v);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < RB; ++j)
-      if (r0 + j < nrhs) partials[(size_t)(r0 + j) * kMaxPartials + blockIdx.x] = v[j];
-    __threadfence();
-    const unsigned t = atomicAdd(counter, 1u);
-    am_last = (t == gridDim.x * gridDim.y - 1);
-  }
-  __syncthreads();
-  return am_last;
-}
-
-// In the last block: tot[r] = sum over blocks of partials[r][.] in block order (deterministic).
-__device__ __forceinline__ void mrhs_totals(int nrhs, const double* partials, double* tot_smem) {
-  __threadfence();
-  for (int r = 0; r < nrhs; ++r) {
-    double s[1] = {0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[0] += __ldcg(partials + (size_t)r * kMaxPartials + b);
-    block_sum<1>(s);
-    if (threadIdx.x == 0) tot_smem[r] = s[0];
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------- K3: p_r = r_r + beta_r p_r
-template <class FieldT>
-__global__ void __launch_bounds__(kBlock) cg_p_mrhs_kernel(int Vh, FieldT r_all, FieldT p_all, int nrhs, CgScalars* sc,
-                                                           double* partials) {
-  using T = typename FieldT::T;
-  const int r = blockIdx.y;
-  double red[1] = {0.0};
-  if (sc[r].done == kRunning) {
-    const FieldT rf = field_at(r_all, r), pf = field_at(p_all, r);
-    const T beta = (T)sc[r].beta;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Vh; k += gridDim.x * blockDim.x) {
-      cvec3<T> rv = rf.load(k), pv = pf.load(k);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        pv.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
-        pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
-      }
-      pf.store(k, pv);
-      red[0] += (double)norm2(pv);
-    }
-  }
-  if (mrhs_arrive<1>(red, r, nrhs, partials, &sc[0].counter[kCtrK3M])) {
-    __shared__ double tot[kMaxRhs];
-    mrhs_totals(nrhs, partials, tot);
-    if (threadIdx.x == 0) {
-      for (int q = 0; q < nrhs; ++q)
-        if (sc[q].done == kRunning) sc[q].pp = tot[q];
-      sc[0].counter[kCtrK3M] = 0u;
-    }
-  }
-}
-
-// ---------------------------------------------------------------- operator kernel with per-RHS epilogue
-template <class LinksT, class FieldT, int RB, class Epi>
-__global__ void __launch_bounds__(kBlock) dslash_mrhs_cg_kernel(Geom g, LinksT U, FieldT in, int nrhs, int out_par,
-                                                                Epi epi) {
-  using T = typename LinksT::T;
-  const int r0 = blockIdx.y * RB;
-  unsigned active = 0;
-#pragma unroll
-  for (int j = 0; j < RB; ++j)
-    if (r0 + j < nrhs && epi.sc[r0 + j].done == kRunning) active |= 1u << j;
-  double red[RB];
-#pragma unroll
-  for (int j = 0; j < RB; ++j) red[j] = 0.0;
-  if (active) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
-      const Site s = site_of(g, k, out_par);
-      int fwd[4], bwd[4];
-      neighbours(g, s, fwd, bwd);
-      cvec3<T> acc[RB];
-#pragma unroll
-      for (int j = 0; j < RB; ++j) zero(acc[j]);
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-        su3<T> Uf = U.load(out_par, mu, k);
-        if constexpr (!LinksT::kFolded) scale(Uf, T(0.5f * fwd_sign(g, s, mu)));
-#pragma unroll
-        for (int j = 0; j < RB; ++j)
-          if ((active >> j) & 1u) mul_add(acc[j], Uf, field_at(in, r0 + j).load(fwd[mu]));
-        su3<T> Ub = U.load(1 - out_par, mu, bwd[mu]);
-        if constexpr (!LinksT::kFolded) scale(Ub, T(0.5f * bwd_sign(g, s, mu)));
-#pragma unroll
-        for (int j = 0; j < RB; ++j)
-          if ((active >> j) & 1u) adj_mul_sub(acc[j], Ub, field_at(in, r0 + j).load(bwd[mu]));
-      }
-#pragma unroll
-      for (int j = 0; j < RB; ++j)
-        if ((active >> j) & 1u) epi.site(k, r0 + j, acc[j], red[j]);
-    }
-  }
-  if (mrhs_arrive<RB>(red, r0, nrhs, epi.partials, &epi.sc[0].counter[Epi::kCounter])) {
-    __shared__ double tot[kMaxRhs];
-    mrhs_totals(nrhs, epi.partials, tot);
-    if (threadIdx.x == 0) {
-      for (int q = 0; q < nrhs; ++q)
-        if (epi.sc[q].done == kRunning) epi.update(q, tot[q]);
-      epi.sc[0].counter[Epi::kCounter] = 0u;
-    }
-  }
-}
-
-// K1: ap_r = D_oe p_r, alpha_r = rr_r / (|ap_r|^2 + m^2 |p_r|^2)
-template <class FieldT>
-struct EpiApM {
-  static constexpr int kCounter = kCtrK1M;
-  FieldT ap;
-  CgScalars* sc;
-  double* partials;
-  template <class T>
-  __device__ __forceinline__ void site(int k, int r, const cvec3<T>& acc, double& red) const {
-    field_at(ap, r).store(k, acc);
-    red += (double)norm2(acc);
-  }
-  __device__ __forceinline__ void update(int r, double apap) const {
-    CgScalars& s = sc[r];
-    const double d = apap + s.m2 * s.pp;
-    const double alpha = s.rr / d;
-    if (!finite_pos(d) || !isfinite(alpha)) s.done = kBreakdown;
-    else s.alpha = alpha;
-  }
-};
-
-// K2: x_r += alpha_r p_r; r_r -= alpha_r (m^2 p_r - D_eo ap_r); beta_r and the exit tests
-template <class FieldT, class XFieldT>
-struct EpiUpdateM {
-  static constexpr int kCounter = kCtrK2M;
-  FieldT p, r;
-  XFieldT x;
-  CgScalars* sc;
-  double* partials;
-  template <class T>
-  __device__ __forceinline__ void site(int k, int q, const cvec3<T>& acc, double& red) const {
-    using TX = typename XFieldT::T;
-    const T alpha = (T)sc[q].alpha, m2 = (T)sc[q].m2;
-    const FieldT pf = field_at(p, q), rf = field_at(r, q);
-    const XFieldT xf = field_at(x, q);
-    const cvec3<T> pv = pf.load(k);
-    cvec3<T> rv = rf.load(k);
-    cvec3<TX> xv = xf.load(k);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const T at_re = fma(m2, pv.c[a].re, -acc.c[a].re);
-      const T at_im = fma(m2, pv.c[a].im, -acc.c[a].im);
-      rv.c[a].re = fma(-alpha, at_re, rv.c[a].re);
-      rv.c[a].im = fma(-alpha, at_im, rv.c[a].im);
-      xv.c[a].re = fma((TX)alpha, (TX)pv.c[a].re, xv.c[a].re);
-      xv.c[a].im = fma((TX)alpha, (TX)pv.c[a].im, xv.c[a].im);
-    }
-    rf.store(k, rv);
-    xf.store(k, xv);
-    red += (double)norm2(rv);
-  }
-  __device__ __forceinline__ void update(int q, double rr) const {
-    CgScalars& s = sc[q];
-    s.iter += 1;
-    s.since_ru += 1;
-    s.rr_prev = s.rr;
-    s.rr = rr;
-    if (!isfinite(rr)) {
-      s.done = kBreakdown;
-      return;
-    }
-    s.beta = rr / s.rr_prev;
-    if (rr > s.rmax2) s.rmax2 = rr;
-    if (rr < s.delit) s.done = kConverged;
-    else if (s.iter >= s.max_iter) s.done = kMaxIter;
-    else if (s.mixed && (s.since_ru >= s.ru_interval || rr < s.delta2 * s.rmax2)) s.done = kReliable;
-  }
-};
-
-// ---------------------------------------------------------------- driver
-template <int PREC, int RECON>
-struct MrhsRunner {
-  using FieldT = Field<PREC>;
-  using XPREC = std::integral_constant<int, PREC == QCD_PREC_DOUBLE ? QCD_PREC_DOUBLE : QCD_PREC_SINGLE>;
-  using XFieldT = Field<XPREC::value>;
-  const qcd_lattice* lat;
-  Geom g;
-  CgWork w;
-  cudaStream_t st;
-  int grid, R, rb;
-  long long launches = 0;
-
-  template <int RB>
-  void launch_ops(const Links<PREC, RECON>& U, FieldT p, FieldT ap, FieldT r, XFieldT x, cudaEvent_t* ev) {
-    const dim3 gr(grid, (R + RB - 1) / RB);
-    if (ev) cudaEventRecord(ev[0], st);
-    dslash_mrhs_cg_kernel<Links<PREC, RECON>, FieldT, RB><<<gr, kBlock, 0, st>>>(
-        g, U, p, R, QCD_ODD, EpiApM<FieldT>{ap, w.sc, w.partials});
-    if (ev) cudaEventRecord(ev[1], st);
-    if (ev) cudaEventRecord(ev[2], st);
-    dslash_mrhs_cg_kernel<Links<PREC, RECON>, FieldT, RB><<<gr, kBlock, 0, st>>>(
-        g, U, ap, R, QCD_EVEN, EpiUpdateM<FieldT, XFieldT>{p, r, x, w.sc, w.partials});
-    if (ev) cudaEventRecord(ev[3], st);
-  }
-
-  int iteration(cudaEvent_t* ev = nullptr) {
-    auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
-    FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh), ap = make_field<PREC>(w.ap, g.Vh);
-    XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
-    cg_p_mrhs_kernel<<<dim3(grid, R), kBlock, 0, st>>>(g.Vh, r, p, R, w.sc, w.partials);
-    switch (rb) {
-      case 1: launch_ops<1>(U, p, ap, r, x, ev); break;
-      case 2: launch_ops<2>(U, p, ap, r, x, ev); break;
-      case 4: launch_ops<4>(U, p, ap, r, x, ev); break;
-      case 8: launch_ops<8>(U, p, ap, r, x, ev); break;
-      case 16: launch_ops<16>(U, p, ap, r, x, ev); break;
-      default: set_error("unsupported RHS block %d", rb); return QCD_ERR_INVALID_ARG;
-    }
-    QCD_CUDA(cudaGetLastError());
-    launches += 3;
-    return QCD_OK;
-  }
-
-  CgRunner<PREC, RECON> single(int r) {
-    CgRunner<PREC, RECON> c;
-    c.lat = lat;
-    c.g = g;
-    c.w = view(w, r);
-    c.st = st;
-    c.grid = grid;
-    return c;
-  }
-};
-
-// Largest RHS block that keeps the register-resident accumulators within budget.
-inline int default_rhs_block(int prec, int R) {
-  const int cap = prec == QCD_PREC_DOUBLE ? 4 : 16;
-  int rb = 1;
-  while (rb * 2 <= R && rb * 2 <= cap) rb *= 2;
-  if (rb < R && rb * 2 <= cap) rb *= 2;  // one partially filled block beats two passes
-  return rb;
-}
-
-template <int PREC, int RECON>
-static int mrhs_typed(qcd_lattice* lat, int R, void* x, const void* b, double mass, double tol, int max_iter,
-                      const qcd_solver_opts& o, void* ws, void* y, qcd_solve_info* info, cudaStream_t st) {
-  MrhsRunner<PREC, RECON> M;
-  M.lat = lat;
-  M.g = make_geom(lat);
-  M.w = carve(lat, PREC, R, (char*)ws);
-  M.st = st;
-  M.grid = site_grid(lat->Vh);
-  M.R = R;
-  M.rb = o.rhs_block;
-  if (M.rb <= 0) {
-    std::vector<int> tuned;
-    M.rb = tune_lookup(mrhs_key(lat, PREC, RECON, R), &tuned) ? tuned[0] : default_rhs_block(PREC, R);
-  }
-  const bool mixed = PREC != QCD_PREC_DOUBLE;
-  const size_t canon_bytes = (size_t)lat->V * 3 * sizeof(double2);
-
-  std::vector<CgScalars> h(R);
-  for (int r = 0; r < R; ++r) {
-    CgScalars s{};
-    s.m2 = mass * mass;
-    s.tol2 = tol * tol;
-    s.max_iter = max_iter;
-    s.ru_interval = o.reliable_interval > 0 ? o.reliable_interval : 100;
-    s.delta2 = o.reliable_delta * o.reliable_delta;
-    s.mixed = mixed ? 1 : 0;
-    h[r] = s;
-  }
-  QCD_CUDA(cudaMemcpyAsync(M.w.sc, h.data(), sizeof(CgScalars) * R, cudaMemcpyHostToDevice, st));
-  int rc = QCD_OK;
-  for (int r = 0; r < R && rc == QCD_OK; ++r) {
-    auto c = M.single(r);
-    rc = c.init((const char*)b + canon_bytes * r);
-    M.launches += c.launches;
-  }
-  if (rc) return rc;
-
-  const int k = o.check_interval > 0 ? o.check_interval : 8;
-  const bool profile = o.profile != 0;
-  std::vector<cudaEvent_t> ev(profile ? 4 * k : 0, nullptr);
-  cudaGraphExec_t exec = nullptr;
-  cudaGraph_t graph = nullptr;
-  auto cleanup = [&]() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    for (auto e : ev)
-      if (e) cudaEventDestroy(e);
-  };
-  for (auto& e : ev) {
-    cudaError_t ce = cudaEventCreate(&e);
-    if (ce != cudaSuccess) { cleanup(); return cuda_fail(ce, "cudaEventCreate"); }
-  }
-  auto ev_at = [&](int i) -> cudaEvent_t* { return profile ? &ev[4 * i] : nullptr; };
-  const bool use_graph = o.use_graph && st != nullptr && !profile;
-  if (use_graph) {
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaStreamBeginCapture"); }
-    const long long before = M.launches;
-    for (int i = 0; i < k && rc == QCD_OK; ++i) rc = M.iteration();
-    M.launches = before;
-    e = cudaStreamEndCapture(st, &graph);
-    if (rc) { cleanup(); return rc; }
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaStreamEndCapture"); }
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaGraphInstantiate"); }
-  }
-
-  int dslash_launches = 0;
-  double dslash_ms = 0.0;
-  if ((rc = read_scalars(M.w, h.data(), st, R))) { cleanup(); return rc; }
-  while (true) {
-    bool any_running = false, any_ru = false;
-    for (int r = 0; r < R; ++r) {
-      const int d = h[r].done;
-      if (mixed && (d == kConverged || d == kReliable)) {
-        auto c = M.single(r);
-        if ((rc = c.reliable_update())) { cleanup(); return rc; }
-        M.launches += c.launches;
-        any_ru = true;
-      }
-    }
-    if (any_ru && (rc = read_scalars(M.w, h.data(), st, R))) { cleanup(); return rc; }
-    for (int r = 0; r < R; ++r) any_running |= h[r].done == kRunning;
-    if (!any_running) break;
-    int iters_before = 0;
-    for (int r = 0; r < R; ++r) iters_before = std::max(iters_before, h[r].iter);
-    if (use_graph) {
-      cudaError_t e = cudaGraphLaunch(exec, st);
-      if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaGraphLaunch"); }
-      M.launches += 3ll * k;
-    } else {
-      for (int i = 0; i < k; ++i)
-        if ((rc = M.iteration(ev_at(i)))) { cleanup(); return rc; }
-    }
-    if ((rc = read_scalars(M.w, h.data(), st, R))) { cleanup(); return rc; }
-    int iters_after = 0;
-    for (int r = 0; r < R; ++r) iters_after = std::max(iters_after, h[r].iter);
-    const int ran = iters_after - iters_before;  // iterations in which some RHS was still active
-    dslash_launches += 2 * ran;
-    if (profile) {
-      for (int i = 0; i < ran && i < k; ++i) {
-        float a = 0.f, c2 = 0.f;
-        cudaError_t e1 = cudaEventElapsedTime(&a, ev[4 * i], ev[4 * i + 1]);
-        cudaError_t e2 = cudaEventElapsedTime(&c2, ev[4 * i + 2], ev[4 * i + 3]);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) { cleanup(); return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaEventElapsedTime"); }
-        dslash_ms += (double)a + (double)c2;
-      }
-    }
-  }
-  cleanup();
-  for (int r = 0; r < R; ++r) {
-    auto c = M.single(r);
-    void* yr = y ? (char*)y + canon_bytes * r : nullptr;
-    if ((rc = c.finish((char*)x + canon_bytes * r, yr))) return rc;
-    M.launches += c.launches;
-  }
-  if ((rc = read_scalars(M.w, h.data(), st, R))) return rc;
-  int status = QCD_OK;
-  for (int r = 0; r < R; ++r) {
-    const CgScalars& s = h[r];
-    const double true_rel = s.bb > 0 ? std::sqrt(s.res2 / s.bb) : 0.0;
-    int st_r = QCD_OK;
-    if (s.done == kBreakdown) st_r = QCD_ERR_BREAKDOWN;
-    else if (s.done == kMaxIter || !(true_rel <= tol)) st_r = QCD_ERR_NOT_CONVERGED;
-    if (st_r == QCD_ERR_BREAKDOWN || (st_r != QCD_OK && status == QCD_OK)) status = st_r;
-    if (info) {
-      qcd_solve_info& I = info[r];
-      I.iterations = s.iter;
-      I.reliable_updates = s.ru_count;
-      I.true_rel_residual = true_rel;
-      I.iterated_rel_residual = s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0;
-      I.converged = st_r == QCD_OK;
-      I.status = st_r;
-      I.kernel_launches = r == 0 ? (int)M.launches : 0;
-      I.dslash_launches = r == 0 ? dslash_launches : 0;
-      I.dslash_ms = r == 0 ? dslash_ms : 0.0;
-    }
-  }
-  return status;
-}
+extern template int mrhs_typed<QCD_PREC_DOUBLE, 18>(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*, qcd_solve_info*, cudaStream_t);
+extern template int mrhs_typed<QCD_PREC_SINGLE, 18>(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*, qcd_solve_info*, cudaStream_t);
+extern template int mrhs_typed<QCD_PREC_SINGLE, 12>(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*, qcd_solve_info*, cudaStream_t);
+extern template int mrhs_typed<QCD_PREC_HALF, 12>(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*, qcd_solve_info*, cudaStream_t);
+extern template int mrhs_typed<QCD_PREC_DF64, 18>(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*, qcd_solve_info*, cudaStream_t);
 
 int run_cg_mrhs(qcd_lattice* lat, int R, void* x, const void* b, double mass, double tol, int max_iter,
                 const qcd_solver_opts& o, void* ws, void* y, qcd_solve_info* info, cudaStream_t st) {
@@ -416,6 +17,7 @@ int run_cg_mrhs(qcd_lattice* lat, int R, void* x, const void* b, double mass, do
   if (prec == QCD_PREC_SINGLE && recon == 18) return mrhs_typed<QCD_PREC_SINGLE, 18>(lat, R, x, b, mass, tol, max_iter, o, ws, y, info, st);
   if (prec == QCD_PREC_SINGLE && recon == 12) return mrhs_typed<QCD_PREC_SINGLE, 12>(lat, R, x, b, mass, tol, max_iter, o, ws, y, info, st);
   if (prec == QCD_PREC_HALF && recon == 12) return mrhs_typed<QCD_PREC_HALF, 12>(lat, R, x, b, mass, tol, max_iter, o, ws, y, info, st);
+  if (prec == QCD_PREC_DF64 && recon == 18) return mrhs_typed<QCD_PREC_DF64, 18>(lat, R, x, b, mass, tol, max_iter, o, ws, y, info, st);
   return QCD_ERR_UNSUPPORTED;
 }
 

@@ -38,20 +38,88 @@ __device__ __forceinline__ cvec3<typename LinksT::T> hop(const Geom& g, const Li
   return acc;
 }
 
+// The four forward hops (sub = 0) or the four backward hops (sub = 1) of site k, written as ONE
+// instruction stream for both lanes of a pair: the link parity and indices are selected, and
+// the backward lane multiplies by -U^dagger (or -s/2 U^dagger) built element by element with
+// selects, so the two lanes of a warp never diverge.
+template <class LinksT, class FieldT>
+__device__ __forceinline__ cvec3<typename LinksT::T> hop_half(const Geom& g, const LinksT& U, const FieldT& in,
+                                                              int out_par, int k, int sub) {
+  using T = typename LinksT::T;
+  const Site s = site_of(g, k, out_par);
+  int fwd[4], bwd[4];
+  neighbours(g, s, fwd, bwd);
+  const int lpar = out_par ^ sub;
+  cvec3<T> acc;
+  zero(acc);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int li = sub ? bwd[mu] : k;
+    const int xi = sub ? bwd[mu] : fwd[mu];
+    const su3<T> L = U.load(lpar, mu, li);
+    const cvec3<T> xv = in.load(xi);
+    su3<T> M;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        M.e[a][b].re = sub ? -L.e[b][a].re : L.e[a][b].re;
+        M.e[a][b].im = sub ? L.e[b][a].im : L.e[a][b].im;
+      }
+    if constexpr (LinksT::kFolded) {
+      mul_add(acc, M, xv);
+    } else {
+      const float sg = sub ? bwd_sign(g, s, mu) : fwd_sign(g, s, mu);
+      axpy(acc, T(0.5f * sg), mul(M, xv));
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ float shfl_pair(float v) { return __shfl_xor_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_pair(double v) { return __shfl_xor_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ df64 shfl_pair(df64 v) { return df64(shfl_pair(v.hi), shfl_pair(v.lo)); }
+
+template <typename T>
+__device__ __forceinline__ void pair_sum(cvec3<T>& acc) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc.c[a].re += shfl_pair(acc.c[a].re);
+    acc.c[a].im += shfl_pair(acc.c[a].im);
+  }
+}
+
 // Epilogue interface:
 //   static constexpr int NV;                        number of FP64 sums reduced over the grid
 //   bool skip() const;                              true -> whole kernel returns at once
 //   void site(int k, cvec3<T>& acc, double* red);   consume the hop result of site k
 //   void finish(double* red);                       grid reduction + scalar update (NV > 0)
-template <class LinksT, class FieldT, class Epi>
+// TPS = threads per output site: 1, or 2 (forward / backward hops on a lane pair, for lattices
+// too small to fill the GPU with one thread per site).
+template <class LinksT, class FieldT, class Epi, int TPS = 1>
 __global__ void __launch_bounds__(kBlock) dslash_kernel(Geom g, LinksT U, FieldT in, int out_par, Epi epi) {
   if (epi.skip()) return;
   double red[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
   for (int j = 0; j < (Epi::NV > 0 ? Epi::NV : 1); ++j) red[j] = 0.0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
-    auto acc = hop(g, U, in, out_par, k);
-    epi.site(k, acc, red);
+  if constexpr (TPS == 1) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
+      auto acc = hop(g, U, in, out_par, k);
+      epi.site(k, acc, red);
+    }
+  } else {
+    // block-uniform trip count: every lane reaches the pair shuffle in every pass
+    const int per_block = blockDim.x >> 1;
+    const int sub = threadIdx.x & 1;
+    for (int base = blockIdx.x * per_block; base < g.Vh; base += gridDim.x * per_block) {
+      const int k = base + (threadIdx.x >> 1);
+      const bool valid = k < g.Vh;
+      cvec3<typename LinksT::T> acc;
+      if (valid) acc = hop_half(g, U, in, out_par, k, sub);
+      else zero(acc);
+      pair_sum(acc);
+      if (valid && sub == 0) epi.site(k, acc, red);
+    }
   }
   if constexpr (Epi::NV > 0) epi.finish(red);
 }
@@ -77,6 +145,8 @@ template <>
 __host__ __device__ inline Field<QCD_PREC_SINGLE> make_field<QCD_PREC_SINGLE>(void* p, int Vh) { return {(float2*)p, Vh}; }
 template <>
 __host__ __device__ inline Field<QCD_PREC_HALF> make_field<QCD_PREC_HALF>(void* p, int Vh) { return {(uint4*)p, Vh}; }
+template <>
+__host__ __device__ inline Field<QCD_PREC_DF64> make_field<QCD_PREC_DF64>(void* p, int Vh) { return {(float4*)p, Vh}; }
 
 template <int PREC, int RECON>
 __host__ __device__ inline Links<PREC, RECON> make_links(const void* p, int Vh);
@@ -87,8 +157,21 @@ __host__ __device__ inline Links<QCD_PREC_SINGLE, 18> make_links<QCD_PREC_SINGLE
 template <>
 __host__ __device__ inline Links<QCD_PREC_SINGLE, 12> make_links<QCD_PREC_SINGLE, 12>(const void* p, int Vh) { return {(const float4*)p, Vh}; }
 template <>
+__host__ __device__ inline Links<QCD_PREC_DF64, 18> make_links<QCD_PREC_DF64, 18>(const void* p, int Vh) { return {(const float4*)p, Vh}; }
+template <>
 __host__ __device__ inline Links<QCD_PREC_HALF, 12> make_links<QCD_PREC_HALF, 12>(const void* p, int Vh) {
   return {(const uint4*)p, (const uint2*)((const uint4*)p + 8 * (size_t)Vh), Vh};
+}
+
+// Two threads per site when one thread per site leaves most of the GPU idle (below about 2
+// blocks of 128 sites per SM, e.g. 16^4 = 32768 sites per parity on 152 SMs) — for the FP32 and
+// FP16 operators only: measured on GB300, the FP64 operator is bound by the FP64 pipe and the
+// pair split (extra selects and shuffles) makes it slower at every size from 8^4 to 24^4.
+inline int threads_per_site(int prec, long long Vh) {
+  if (prec == QCD_PREC_DOUBLE) return 1;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return Vh < (long long)sms * kBlock * 2 ? 2 : 1;
 }
 
 // Field r of a multi-RHS packed field (nrhs fields back to back).
@@ -113,6 +196,22 @@ inline int site_grid(long long Vh) {
   long long b = (Vh + kBlock - 1) / kBlock;
   const long long cap = kMaxPartials;
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+// Grid for kernels that end in a grid-wide reduction: at most one wave of resident blocks
+// (SMs x blocks per SM of `kernel`), each looping over sites. Every block pays the end-of-block
+// barrier and partial write once per launch instead of once per wave of blocks.
+template <class KernelT>
+inline int one_wave_grid(long long Vh, KernelT kernel, int tps = 1) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return site_grid(Vh);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  const long long wave = (long long)sms * per_sm;
+  const long long need = (Vh * tps + kBlock - 1) / kBlock;
+  long long g = need < wave ? need : wave;
+  if (g > kMaxPartials) g = kMaxPartials;
+  return (int)(g > 0 ? g : 1);
 }
 
 }  // namespace qcd

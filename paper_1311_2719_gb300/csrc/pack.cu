@@ -26,6 +26,13 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, voi
         double2* o = (double2*)out + (size_t)pm * 9 * g.Vh + k;
 #pragma unroll
         for (int i = 0; i < 9; ++i) o[(size_t)i * g.Vh] = e[i];
+      } else if constexpr (PREC == QCD_PREC_DF64) {
+        float4* o = (float4*)out + (size_t)pm * 9 * g.Vh + k;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const df64 re(e[i].x), im(e[i].y);
+          o[(size_t)i * g.Vh] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
       } else {
         float2* o = (float2*)out + (size_t)pm * 9 * g.Vh + k;
 #pragma unroll
@@ -60,6 +67,7 @@ int launch_pack_links(const qcd_lattice* lat, const void* canon, void* out, int 
   else if (prec == QCD_PREC_SINGLE && recon == 18) pack_links_kernel<QCD_PREC_SINGLE, 18><<<grid, 256, 0, st>>>(g, c, out);
   else if (prec == QCD_PREC_SINGLE && recon == 12) pack_links_kernel<QCD_PREC_SINGLE, 12><<<grid, 256, 0, st>>>(g, c, out);
   else if (prec == QCD_PREC_HALF && recon == 12) pack_links_kernel<QCD_PREC_HALF, 12><<<grid, 256, 0, st>>>(g, c, out);
+  else if (prec == QCD_PREC_DF64 && recon == 18) pack_links_kernel<QCD_PREC_DF64, 18><<<grid, 256, 0, st>>>(g, c, out);
   else return QCD_ERR_UNSUPPORTED;
   QCD_CUDA(cudaGetLastError());
   return QCD_OK;
@@ -99,6 +107,7 @@ int launch_pack_field(const qcd_lattice* lat, void* packed, const void* canon, i
     case QCD_PREC_DOUBLE: pack_field_kernel<<<grid, kBlock, 0, st>>>(g, make_field<QCD_PREC_DOUBLE>(packed, g.Vh), c, par); break;
     case QCD_PREC_SINGLE: pack_field_kernel<<<grid, kBlock, 0, st>>>(g, make_field<QCD_PREC_SINGLE>(packed, g.Vh), c, par); break;
     case QCD_PREC_HALF: pack_field_kernel<<<grid, kBlock, 0, st>>>(g, make_field<QCD_PREC_HALF>(packed, g.Vh), c, par); break;
+    case QCD_PREC_DF64: pack_field_kernel<<<grid, kBlock, 0, st>>>(g, make_field<QCD_PREC_DF64>(packed, g.Vh), c, par); break;
     default: return QCD_ERR_INVALID_ARG;
   }
   QCD_CUDA(cudaGetLastError());
@@ -114,6 +123,7 @@ int launch_unpack_field(const qcd_lattice* lat, void* canon, const void* packed,
     case QCD_PREC_DOUBLE: unpack_field_kernel<<<grid, kBlock, 0, st>>>(g, c, make_field<QCD_PREC_DOUBLE>(p, g.Vh), par); break;
     case QCD_PREC_SINGLE: unpack_field_kernel<<<grid, kBlock, 0, st>>>(g, c, make_field<QCD_PREC_SINGLE>(p, g.Vh), par); break;
     case QCD_PREC_HALF: unpack_field_kernel<<<grid, kBlock, 0, st>>>(g, c, make_field<QCD_PREC_HALF>(p, g.Vh), par); break;
+    case QCD_PREC_DF64: unpack_field_kernel<<<grid, kBlock, 0, st>>>(g, c, make_field<QCD_PREC_DF64>(p, g.Vh), par); break;
     default: return QCD_ERR_INVALID_ARG;
   }
   QCD_CUDA(cudaGetLastError());

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "../../include/qcd.h"
+#include "df64.cuh"
 
 namespace qcd {
 
@@ -31,7 +32,7 @@ struct qcd_lattice {
   long long Vh;
   int tbc;
   int device;
-  qcd::LinkSet links[3];  // indexed by precision
+  qcd::LinkSet links[4];  // indexed by precision
 };
 
 namespace qcd {
@@ -334,13 +335,47 @@ struct Field<QCD_PREC_HALF> {
   static size_t bytes(long long Vh) { return (size_t)Vh * sizeof(uint4); }
 };
 
+// FP64-accuracy field as float-float pairs: float4 {re.hi, re.lo, im.hi, im.lo} per colour.
+template <>
+struct Field<QCD_PREC_DF64> {
+  using T = df64;
+  static constexpr int kElemsPerSite = 3;
+  float4* p;  // [3][Vh]
+  int Vh;
+  __device__ __forceinline__ static cvec3<df64> decode3(float4 a, float4 b, float4 c) {
+    cvec3<df64> v;
+    v.c[0].re = df64(a.x, a.y); v.c[0].im = df64(a.z, a.w);
+    v.c[1].re = df64(b.x, b.y); v.c[1].im = df64(b.z, b.w);
+    v.c[2].re = df64(c.x, c.y); v.c[2].im = df64(c.z, c.w);
+    return v;
+  }
+  __device__ __forceinline__ cvec3<df64> load(int k) const {
+    return decode3(__ldg(p + k), __ldg(p + (size_t)Vh + k), __ldg(p + 2 * (size_t)Vh + k));
+  }
+  __device__ __forceinline__ cvec3<df64> load_cg(int k) const {
+    return decode3(__ldcg(p + k), __ldcg(p + (size_t)Vh + k), __ldcg(p + 2 * (size_t)Vh + k));
+  }
+  __device__ __forceinline__ void store(int k, const cvec3<df64>& v) const {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      p[(size_t)a * Vh + k] = make_float4(v.c[a].re.hi, v.c[a].re.lo, v.c[a].im.hi, v.c[a].im.lo);
+  }
+  static size_t bytes(long long Vh) { return (size_t)Vh * 3 * sizeof(float4); }
+};
+
 inline size_t field_bytes(int prec, long long Vh) {
   switch (prec) {
     case QCD_PREC_DOUBLE: return Field<QCD_PREC_DOUBLE>::bytes(Vh);
     case QCD_PREC_SINGLE: return Field<QCD_PREC_SINGLE>::bytes(Vh);
     case QCD_PREC_HALF: return Field<QCD_PREC_HALF>::bytes(Vh);
+    case QCD_PREC_DF64: return Field<QCD_PREC_DF64>::bytes(Vh);
   }
   return 0;
+}
+
+// Precision of the CG solution accumulator for an inner precision.
+__host__ __device__ constexpr int x_prec(int prec) {
+  return prec == QCD_PREC_DOUBLE ? QCD_PREC_DOUBLE : (prec == QCD_PREC_DF64 ? QCD_PREC_DF64 : QCD_PREC_SINGLE);
 }
 
 // A field whose loads go to L2 (coherent), for data that other blocks write during the same
@@ -442,11 +477,32 @@ struct Links<QCD_PREC_HALF, 12> {
   static size_t bytes(long long Vh) { return (size_t)2 * 4 * Vh * (sizeof(uint4) + sizeof(uint2)); }
 };
 
+template <>
+struct Links<QCD_PREC_DF64, 18> {
+  using T = df64;
+  static constexpr bool kFolded = true;
+  const float4* p;  // [2][4][9][Vh] of {re.hi, re.lo, im.hi, im.lo}
+  int Vh;
+  __device__ __forceinline__ su3<df64> load(int par, int mu, int k) const {
+    su3<df64> U;
+    const float4* b = p + (size_t)(par * 4 + mu) * 9 * Vh + k;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float4 d = __ldg(b + (size_t)e * Vh);
+      U.e[e / 3][e % 3].re = df64(d.x, d.y);
+      U.e[e / 3][e % 3].im = df64(d.z, d.w);
+    }
+    return U;
+  }
+  static size_t bytes(long long Vh) { return (size_t)2 * 4 * 9 * Vh * sizeof(float4); }
+};
+
 inline size_t links_bytes(int prec, int recon, long long Vh) {
   if (prec == QCD_PREC_DOUBLE && recon == 18) return Links<QCD_PREC_DOUBLE, 18>::bytes(Vh);
   if (prec == QCD_PREC_SINGLE && recon == 18) return Links<QCD_PREC_SINGLE, 18>::bytes(Vh);
   if (prec == QCD_PREC_SINGLE && recon == 12) return Links<QCD_PREC_SINGLE, 12>::bytes(Vh);
   if (prec == QCD_PREC_HALF && recon == 12) return Links<QCD_PREC_HALF, 12>::bytes(Vh);
+  if (prec == QCD_PREC_DF64 && recon == 18) return Links<QCD_PREC_DF64, 18>::bytes(Vh);
   return 0;
 }
 

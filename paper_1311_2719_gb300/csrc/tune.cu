@@ -120,7 +120,7 @@ int qcd_tune_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, do
   std::vector<qcd_solve_info> info(nrhs);
   for (int rb : cands) {
     if (rb > 2 * nrhs && rb > 1) break;
-    if (o.prec_inner == QCD_PREC_DOUBLE && rb > 4) break;  // register budget of FP64 accumulators
+    if ((o.prec_inner == QCD_PREC_DOUBLE || o.prec_inner == QCD_PREC_DF64) && rb > 4) break;  // 64-bit accumulators
     o.rhs_block = rb;
     // a short run of the real solve (it stops at max_iter; only the launch timings matter)
     const int rc = run_cg_mrhs(lat, nrhs, x_dev, b_dev, mass, 1e-14, 24, o, workspace_dev, nullptr, info.data(),

@@ -27,8 +27,8 @@ QCD_ERR_UNSUPPORTED = 6
 QCD_ERR_NO_LINKS = 7
 
 QCD_EVEN, QCD_ODD = 0, 1
-QCD_PREC_DOUBLE, QCD_PREC_SINGLE, QCD_PREC_HALF = 0, 1, 2
-PREC_NAMES = {"double": QCD_PREC_DOUBLE, "single": QCD_PREC_SINGLE, "half": QCD_PREC_HALF}
+QCD_PREC_DOUBLE, QCD_PREC_SINGLE, QCD_PREC_HALF, QCD_PREC_DF64 = 0, 1, 2, 3
+PREC_NAMES = {"double": QCD_PREC_DOUBLE, "single": QCD_PREC_SINGLE, "half": QCD_PREC_HALF, "df64": QCD_PREC_DF64}
 
 
 class QcdError(RuntimeError):

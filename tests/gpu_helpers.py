@@ -4,9 +4,9 @@ import numpy as np
 from paper_1311_2719_gb300 import qcd as Q
 
 PRECS = {"double": (Q.QCD_PREC_DOUBLE, 18), "single18": (Q.QCD_PREC_SINGLE, 18),
-         "single12": (Q.QCD_PREC_SINGLE, 12), "half12": (Q.QCD_PREC_HALF, 12)}
-# relative-L2 bars of the half-lattice operator against the FP64 oracle
-TOL = {"double": 1e-12, "single18": 1e-5, "single12": 1e-5, "half12": 5e-3}
+         "single12": (Q.QCD_PREC_SINGLE, 12), "half12": (Q.QCD_PREC_HALF, 12), "df64": (Q.QCD_PREC_DF64, 18)}
+# relative-L2 bars of the half-lattice operator against the FP64 oracle (df64 is held to FP64's)
+TOL = {"double": 1e-12, "single18": 1e-5, "single12": 1e-5, "half12": 5e-3, "df64": 1e-12}
 
 
 def rel(a, b):

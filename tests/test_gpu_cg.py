@@ -65,7 +65,7 @@ def test_graph_replay_equals_eager_bitwise(H):
         assert np.array_equal(x1, x3)
 
 
-@pytest.mark.parametrize("inner", ["single18", "single12", "half12"])
+@pytest.mark.parametrize("inner", ["single18", "single12", "half12", "df64"])
 @pytest.mark.parametrize("dims,m", [((8, 8, 8, 8), 0.1), ((6, 6, 6, 6), 0.02)])
 def test_mixed_precision_cg_reaches_fp64_residual(H, inner, dims, m):
     U = I.make_links(dims, kind="haar", seed=1)
@@ -133,3 +133,18 @@ def test_full_size_32_4_mixed(H, inner):
     sites = cand[S.parity_of_sites(dims, cand) == 0][:2000]
     r = b[sites] - S.mdagm_sites(U, x, dims, m, sites)
     assert np.linalg.norm(r) / np.linalg.norm(b[sites]) <= 3e-10
+
+
+def test_df64_cg_full_size_16_4(H):
+    """16^4, m = 0.1: the df64 recursion (FP32 pipes, 48-bit significand) with FP64 confirmation."""
+    dims, m = (16, 16, 16, 16), 0.1
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    rig = H.Rig(dims, U, precs=["double", "df64"])
+    rc, info, x, y = rig.cg(b, m, tol=1e-10, inner="df64")
+    assert rc == Q.QCD_OK and info["true_rel_residual"] <= 1e-10
+    assert S.true_residual(U, x, b, dims, m) <= 1.01e-10
+    _, info64, x64, _ = rig.cg(b, m, tol=1e-10)
+    # same recursion up to rounding: iteration counts within a few, solutions to ~kappa * tol
+    assert abs(info["iterations"] - info64["iterations"]) <= 5
+    assert H.rel(x, x64) <= 1e-8

@@ -9,7 +9,7 @@ pytestmark = pytest.mark.gpu
 
 # several 128-site blocks with a ragged tail, asymmetric extents, the degenerate L = 2 case
 SMALL = [(2, 2, 2, 2), (4, 4, 4, 4), (2, 4, 6, 8), (6, 6, 6, 6), (10, 4, 6, 8), (8, 6, 4, 2)]
-ALL_PRECS = ["double", "single18", "single12", "half12"]
+ALL_PRECS = ["double", "single18", "single12", "half12", "df64"]
 
 
 @pytest.fixture(scope="module")
@@ -88,11 +88,16 @@ def test_pack_unpack_round_trip(H):
         scale = np.max(np.abs(np.stack([x.real, x.imag], -1)), axis=(1, 2))
         err = np.max(np.abs(np.stack([(back - x).real, (back - x).imag], -1)), axis=(1, 2))
         assert np.all(err[mask] <= scale[mask] * 2.0 ** -11 * 1.0001)
+        # df64: hi = fl32(v), lo = fl32(v - hi): |error| <= 2^-48 |v| per component
+        f = rig.pack(xd, par, 3)
+        back = H.host(rig.unpack(f, par, 3))
+        assert np.all(np.abs((back - x).real[mask]) <= 2.0 ** -47 * np.abs(x.real[mask]) + 1e-300)
+        assert np.all(np.abs((back - x).imag[mask]) <= 2.0 ** -47 * np.abs(x.imag[mask]) + 1e-300)
     del torch
 
 
 @pytest.mark.parametrize("nrhs", [1, 3, 8, 16])
-@pytest.mark.parametrize("name", ["double", "single12", "half12"])
+@pytest.mark.parametrize("name", ["double", "single12", "half12", "df64"])
 def test_multi_rhs_matches_oracle(H, nrhs, name):
     dims = (6, 4, 4, 8)
     U = I.make_links(dims, kind="haar", seed=1)
@@ -107,11 +112,12 @@ def test_full_size_16_4_double_whole_lattice(H):
     dims = (16, 16, 16, 16)
     U = I.make_links(dims, kind="haar", seed=1)
     x = I.make_source(dims, seed=2)
-    rig = H.Rig(dims, U, precs=["double", "single18"])
+    rig = H.Rig(dims, U, precs=["double", "single18", "df64"])
     for par in (0, 1):
         want = S.dslash_parity(U, x, dims, par)
         assert H.rel(rig.dslash(x, par, "double"), want) <= 1e-12
         assert H.rel(rig.dslash(x, par, "single18"), want) <= 1e-5
+        assert H.rel(rig.dslash(x, par, "df64"), want) <= 1e-12
 
 
 def _sample_sites(dims, par, n, seed):
@@ -125,7 +131,7 @@ def _sample_sites(dims, par, n, seed):
     return np.unique(np.concatenate([cand, edge]))
 
 
-@pytest.mark.parametrize("name", ["double", "single12", "half12"])
+@pytest.mark.parametrize("name", ["double", "single12", "half12", "df64"])
 def test_full_size_32_4_sampled_sites(H, name):
     """32^4 (the mixed-precision workload): every output computed, sampled sites checked."""
     dims = (32, 32, 32, 32)
