@@ -25,6 +25,41 @@
 
 namespace qcd {
 
+// Build the device-side solve loop: graph = { WHILE(cond) { k x (K3, K1, K2); gated reliable
+// update; control } }. The condition starts at 1 on every launch; the control kernel clears it
+// when the recursion stops (converged on the true residual, max_iter, breakdown) or after a
+// guard number of passes.
+template <int PREC, int RECON>
+static int device_loop(CgRunner<PREC, RECON>& R, int k, int max_iter, cudaGraphExec_t& exec, cudaGraph_t& graph) {
+  QCD_CUDA(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  QCD_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams params = {};
+  params.type = cudaGraphNodeTypeConditional;
+  params.conditional.handle = handle;
+  params.conditional.type = cudaGraphCondTypeWhile;
+  params.conditional.size = 1;
+  cudaGraphNode_t node;
+  QCD_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &params));
+  cudaGraph_t body = params.conditional.phGraph_out[0];
+  QCD_CUDA(cudaStreamBeginCaptureToGraph(R.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int rc = QCD_OK;
+  for (int i = 0; i < k && rc == QCD_OK; ++i) rc = R.iteration();
+  if (rc == QCD_OK) rc = R.reliable_update(true);
+  const int max_loops = max_iter / k + 2 * (max_iter / 100 + 1) + 16;
+  if (rc == QCD_OK) {
+    cg_loop_control_kernel<<<1, 1, 0, R.st>>>(R.w.sc, handle, max_loops);
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) rc = cuda_fail(le, "cg_loop_control_kernel");
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(R.st, &captured);
+  if (rc) return rc;
+  QCD_CUDA(e);
+  QCD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  return QCD_OK;
+}
+
 template <int PREC, int RECON>
 static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, double tol, int max_iter,
                     const qcd_solver_opts& o, void* ws, void* y, qcd_solve_info* info, cudaStream_t st) {
@@ -66,24 +101,25 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
   auto ev_at = [&](int i) -> cudaEvent_t* { return profile ? &ev[4 * i] : nullptr; };
   // Events recorded inside a graph cannot be timed, so profiling runs the chunk as direct launches.
   const bool use_graph = o.use_graph && st != nullptr && !profile;
-  if (use_graph) {
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaStreamBeginCapture"); }
-    const long long before = R.launches;
-    for (int i = 0; i < k && rc == QCD_OK; ++i) rc = R.iteration(ev_at(i));
-    R.launches = before;  // counted when the graph is replayed
-    e = cudaStreamEndCapture(st, &graph);
-    if (rc) { cleanup(); return rc; }
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaStreamEndCapture"); }
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaGraphInstantiate"); }
-  }
-
   int status = QCD_OK;
   int dslash_launches = 0;
   double dslash_ms = 0.0;
-  if ((rc = read_scalars(R.w, &h, st))) { cleanup(); return rc; }
-  while (true) {
+  if (use_graph) {
+    // The whole solve loop is ONE graph launch: a conditional WHILE node whose body runs k
+    // iterations, the (flag-gated) reliable update and the control kernel that decides whether
+    // to loop again. The host waits once, at the end.
+    if ((rc = device_loop(R, k, max_iter, exec, graph))) { cleanup(); return rc; }
+    cudaError_t e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaGraphLaunch"); }
+    if ((rc = read_scalars(R.w, &h, st))) { cleanup(); return rc; }
+    if (h.done == kBreakdown) status = QCD_ERR_BREAKDOWN;
+    else if (h.done != kTrueConverged) status = QCD_ERR_NOT_CONVERGED;
+    R.launches += (long long)h.loops * (3ll * k + (mixed ? 3 : 2) + 1);
+    dslash_launches = 2 * h.iter;
+  } else {
+    if ((rc = read_scalars(R.w, &h, st))) { cleanup(); return rc; }
+  }
+  while (!use_graph) {
     if (h.done == kBreakdown) { status = QCD_ERR_BREAKDOWN; break; }
     if (h.done == kMaxIter) { status = QCD_ERR_NOT_CONVERGED; break; }
     if (h.done == kTrueConverged) break;
@@ -95,14 +131,8 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
     }
     if (h.iter >= max_iter) { status = QCD_ERR_NOT_CONVERGED; break; }
     const int iter_before = h.iter;
-    if (use_graph) {
-      cudaError_t e = cudaGraphLaunch(exec, st);
-      if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaGraphLaunch"); }
-      R.launches += 3ll * k;
-    } else {
-      for (int i = 0; i < k; ++i) {
-        if ((rc = R.iteration(ev_at(i)))) { cleanup(); return rc; }
-      }
+    for (int i = 0; i < k; ++i) {
+      if ((rc = R.iteration(ev_at(i)))) { cleanup(); return rc; }
     }
     if ((rc = read_scalars(R.w, &h, st))) { cleanup(); return rc; }
     // the iterations that did work in this chunk: the rest returned at once on the done flag

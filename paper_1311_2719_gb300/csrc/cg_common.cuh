@@ -12,7 +12,7 @@ namespace qcd {
 
 struct __align__(256) CgScalars {
   double rr, rr_prev, pp, alpha, beta, delit, bb, m2, res2, rmax2, delta2, tol2;
-  int iter, max_iter, done, since_ru, ru_count, ru_interval, mixed, pad;
+  int iter, max_iter, done, since_ru, ru_count, ru_interval, mixed, loops;
   unsigned counter[16];
 };
 static_assert(sizeof(CgScalars) <= 256, "scalars block");
@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(kBlock) cg_init_kernel(Geom g, const double2* 
     sc->iter = 0;
     sc->since_ru = 0;
     sc->ru_count = 0;
+    sc->loops = 0;
     sc->done = !isfinite(bb) ? kBreakdown : (bb == 0.0 ? kTrueConverged : kRunning);
   }
 }
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(kBlock) cg_p_kernel(int Vh, FieldT r, FieldT p
 template <class FieldT>
 struct EpiAp {
   static constexpr int NV = 1;
+  static constexpr bool kPrefetch = false;
   FieldT ap;
   CgScalars* sc;
   double* partials;
@@ -127,18 +129,26 @@ struct EpiAp {
 template <class FieldT, class XFieldT>
 struct EpiUpdate {
   static constexpr int NV = 1;
+  static constexpr bool kPrefetch = true;
   FieldT p, r;
   XFieldT x;
   CgScalars* sc;
   double* partials;
+  struct Pre {
+    cvec3<typename FieldT::T> p, r;
+    cvec3<typename XFieldT::T> x;
+  };
   __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
+  __device__ __forceinline__ Pre prefetch(int k) const { return Pre{p.load(k), r.load(k), x.load(k)}; }
   template <class T>
-  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double* red) const {
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double* red) const { site_pre(k, acc, red, prefetch(k)); }
+  template <class T>
+  __device__ __forceinline__ void site_pre(int k, cvec3<T>& acc, double* red, const Pre& pre) const {
     using TX = typename XFieldT::T;
     const T alpha = (T)sc->alpha, m2 = (T)sc->m2;
-    const cvec3<T> pv = p.load(k);
-    cvec3<T> rv = r.load(k);
-    cvec3<TX> xv = x.load(k);
+    const cvec3<T>& pv = pre.p;
+    cvec3<T> rv = pre.r;
+    cvec3<TX> xv = pre.x;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const T at_re = fma(m2, pv.c[a].re, -acc.c[a].re);  // (A p)_a = m^2 p - D_eo D_oe p
@@ -178,10 +188,19 @@ struct EpiUpdate {
 };
 
 // ---------------------------------------------------------------- reliable update (FP64)
-// x_hi += x_lo, x_lo = 0
+// True when the recursion asks for a reliable update: it met tol (confirm on the true residual)
+// or, mixed only, the periodic / delta test fired.
+__device__ __forceinline__ bool ru_wanted(const CgScalars* sc) {
+  const int d = sc->done;
+  return d == kConverged || (sc->mixed && d == kReliable);
+}
+
+// x_hi += x_lo, x_lo = 0. With `gate`, the kernel returns at once unless ru_wanted(gate).
 template <class XFieldT>
-__global__ void __launch_bounds__(kBlock) ru_accumulate_kernel(int Vh, Field<QCD_PREC_DOUBLE> x_hi, XFieldT x_lo) {
+__global__ void __launch_bounds__(kBlock) ru_accumulate_kernel(int Vh, Field<QCD_PREC_DOUBLE> x_hi, XFieldT x_lo,
+                                                               const CgScalars* gate = nullptr) {
   using TX = typename XFieldT::T;
+  if (gate && !ru_wanted(gate)) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Vh; k += gridDim.x * blockDim.x) {
     cvec3<double> xh = x_hi.load(k);
     const cvec3<TX> xl = x_lo.load(k);
@@ -198,6 +217,7 @@ __global__ void __launch_bounds__(kBlock) ru_accumulate_kernel(int Vh, Field<QCD
 template <class FieldT>
 struct EpiReliable {
   static constexpr int NV = 1;
+  static constexpr bool kPrefetch = false;
   Field<QCD_PREC_DOUBLE> b, x;
   FieldT r_lo;
   CgScalars* sc;
@@ -240,9 +260,31 @@ struct EpiReliable {
   }
 };
 
+// An epilogue that runs only when a reliable update is wanted (for the device-side solve loop,
+// where the update kernels sit in every pass of the loop body and return at once otherwise).
+template <class Epi>
+struct Gated {
+  static constexpr int NV = Epi::NV;
+  static constexpr bool kPrefetch = false;
+  Epi epi;
+  const CgScalars* gate;
+  __device__ __forceinline__ bool skip() const { return !ru_wanted(gate) || epi.skip(); }
+  template <class T>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double* red) const { epi.site(k, acc, red); }
+  __device__ __forceinline__ void finish(double* red) const { epi.finish(red); }
+};
+
+// Last node of the device-side solve loop: keep looping while the recursion runs (bounded by
+// `max_loops` passes as a guard).
+static __global__ void cg_loop_control_kernel(CgScalars* sc, cudaGraphConditionalHandle handle, int max_loops) {
+  const int loops = ++sc->loops;
+  cudaGraphSetConditional(handle, (sc->done == kRunning && loops < max_loops) ? 1u : 0u);
+}
+
 // Final true residual: res = b - (m^2 x - D_eo y), y = D_oe x.
 struct EpiResidual {
   static constexpr int NV = 1;
+  static constexpr bool kPrefetch = false;
   Field<QCD_PREC_DOUBLE> b, x;
   CgScalars* sc;
   double* partials;
@@ -397,16 +439,25 @@ struct CgRunner {
   // Replace the iterated residual by the true one, r = b - A x_hi in FP64 (mixed: after folding
   // x_lo into x_hi). Plain FP64 runs it once the recursion meets tol, to confirm on the true
   // residual; the mixed solver also every reliable_interval iterations / on the delta test.
-  int reliable_update() {
+  // `gated`: every kernel checks the device flag first (for the device-side loop body).
+  int reliable_update(bool gated = false) {
     auto U64 = make_links<QCD_PREC_DOUBLE, 18>(lat->links[QCD_PREC_DOUBLE].ptr, g.Vh);
     auto xh = make_field<QCD_PREC_DOUBLE>(w.x_hi, g.Vh);
     auto tmp = make_field<QCD_PREC_DOUBLE>(w.tmp_o, g.Vh);
     launches += PREC != QCD_PREC_DOUBLE ? 3 : 2;
     if (PREC != QCD_PREC_DOUBLE)  // plain FP64: x_lo is x_hi itself
-      ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh));
-    op(U64, xh, QCD_ODD, EpiStore<Field<QCD_PREC_DOUBLE>>{tmp});
-    op(U64, tmp, QCD_EVEN,
-       EpiReliable<FieldT>{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, make_field<PREC>(w.r, g.Vh), w.sc, w.partials});
+      ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh),
+                                                    gated ? w.sc : nullptr);
+    EpiStore<Field<QCD_PREC_DOUBLE>> store{tmp};
+    EpiReliable<FieldT> rel{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, make_field<PREC>(w.r, g.Vh), w.sc,
+                            w.partials};
+    if (gated) {
+      op(U64, xh, QCD_ODD, Gated<decltype(store)>{store, w.sc});
+      op(U64, tmp, QCD_EVEN, Gated<decltype(rel)>{rel, w.sc});
+    } else {
+      op(U64, xh, QCD_ODD, store);
+      op(U64, tmp, QCD_EVEN, rel);
+    }
     QCD_CUDA(cudaGetLastError());
     return QCD_OK;
   }

@@ -8,6 +8,7 @@ namespace qcd {
 template <class FieldT>
 struct EpiMdagm {
   static constexpr int NV = 0;
+  static constexpr bool kPrefetch = false;
   FieldT in, out;
   double m2;
   __device__ __forceinline__ bool skip() const { return false; }

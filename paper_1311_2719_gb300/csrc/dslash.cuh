@@ -3,6 +3,8 @@
 // the paper's congrad, §4).
 #pragma once
 
+#include <type_traits>
+
 #include "qcd_internal.cuh"
 
 namespace qcd {
@@ -91,21 +93,42 @@ __device__ __forceinline__ void pair_sum(cvec3<T>& acc) {
 
 // Epilogue interface:
 //   static constexpr int NV;                        number of FP64 sums reduced over the grid
+//   static constexpr bool kPrefetch;                true: prefetch(k) / site_pre(k, acc, red, pre)
+//                                                   are used on the one-thread-per-site path
 //   bool skip() const;                              true -> whole kernel returns at once
 //   void site(int k, cvec3<T>& acc, double* red);   consume the hop result of site k
 //   void finish(double* red);                       grid reduction + scalar update (NV > 0)
 // TPS = threads per output site: 1, or 2 (forward / backward hops on a lane pair, for lattices
 // too small to fill the GPU with one thread per site).
+// Resident blocks per SM the operator kernels are compiled for: 8 (<= 64 registers) for the
+// FP32-arithmetic operators, which are bound by memory latency and need the warps (measured on
+// GB300: the reduction epilogues otherwise take 96 registers and half the occupancy); 5 for FP64
+// and 4 for df64, whose 64-bit operands need the registers.
+template <class LinksT>
+struct MinBlocks {
+  static constexpr int value =
+      sizeof(typename LinksT::T) == 4 ? 8 : (std::is_same<typename LinksT::T, double>::value ? 5 : 4);
+};
+
 template <class LinksT, class FieldT, class Epi, int TPS = 1>
-__global__ void __launch_bounds__(kBlock) dslash_kernel(Geom g, LinksT U, FieldT in, int out_par, Epi epi) {
+__global__ void __launch_bounds__(kBlock, MinBlocks<LinksT>::value) dslash_kernel(Geom g, LinksT U, FieldT in,
+                                                                                 int out_par, Epi epi) {
   if (epi.skip()) return;
   double red[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
   for (int j = 0; j < (Epi::NV > 0 ? Epi::NV : 1); ++j) red[j] = 0.0;
   if constexpr (TPS == 1) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
-      auto acc = hop(g, U, in, out_par, k);
-      epi.site(k, acc, red);
+      if constexpr (Epi::kPrefetch) {
+        // the epilogue's own-site operands are loaded before the hop so that their latency
+        // overlaps the neighbour gathers instead of following them
+        const auto pre = epi.prefetch(k);
+        auto acc = hop(g, U, in, out_par, k);
+        epi.site_pre(k, acc, red, pre);
+      } else {
+        auto acc = hop(g, U, in, out_par, k);
+        epi.site(k, acc, red);
+      }
     }
   } else {
     // block-uniform trip count: every lane reaches the pair shuffle in every pass
@@ -128,6 +151,7 @@ __global__ void __launch_bounds__(kBlock) dslash_kernel(Geom g, LinksT U, FieldT
 template <class FieldT>
 struct EpiStore {
   static constexpr int NV = 0;
+  static constexpr bool kPrefetch = false;
   FieldT out;
   __device__ __forceinline__ bool skip() const { return false; }
   template <class T>
