@@ -222,7 +222,7 @@ int qcd_dslash_mrhs(const qcd_lattice* lat, void* out_dev, const void* in_dev, i
   if (out_parity != QCD_EVEN && out_parity != QCD_ODD) return invalid("out_parity must be 0 or 1");
   if (int rc = check_links(lat, prec)) return rc;
   int rb = 1;
-  while (rb * 2 <= nrhs && rb < (prec == QCD_PREC_DOUBLE || prec == QCD_PREC_DF64 ? 4 : 8)) rb *= 2;
+  while (rb * 2 <= nrhs && rb < 4) rb *= 2;
   return launch_dslash_mrhs(lat, out_dev, in_dev, nrhs, out_parity, prec, rb, as_stream(stream));
 }
 

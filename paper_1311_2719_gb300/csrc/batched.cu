@@ -52,35 +52,39 @@ struct BatchResult {
 
 enum { kBatchOk = 0, kBatchMaxIter = 1, kBatchBreakdown = 2 };
 
-// Cluster-wide deterministic sum of NV values (see the file comment). `slots` is double-buffered.
-template <int NV>
-__device__ __forceinline__ void cluster_sum(double (&v)[NV], double (*slots)[4], int& buf,
-                                            const cg::cluster_group& cluster) {
-  block_sum<NV>(v);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) slots[buf][j] = v[j];
-  }
-  __threadfence();  // global writes of this phase before the barrier
+// Cluster-wide deterministic sum (see the file comment). Every thread passes its partial; the
+// total is returned in thread 0 of each CTA only (each CTA's thread 0 adds the same C block
+// sums in rank order, so all of them hold the same bits). `slots` is double-buffered: a slot is
+// rewritten two reductions later, after every CTA has passed the barrier of the one between.
+__device__ __forceinline__ double cluster_total(double part, double* slots, int& buf,
+                                                const cg::cluster_group& cluster) {
+  double v[1] = {part};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) slots[buf] = v[0];
+  // make this phase's global writes visible to the cluster before its barrier
+  asm volatile("fence.acq_rel.cluster;" ::: "memory");
   cluster.sync();
-  double t[NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) t[j] = 0.0;
-  const int C = (int)cluster.num_blocks();
-  for (int r = 0; r < C; ++r) {
-    const double* s = cluster.map_shared_rank(&slots[buf][0], r);
-#pragma unroll
-    for (int j = 0; j < NV; ++j) t[j] += s[j];
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    const int C = (int)cluster.num_blocks();
+    for (int r = 0; r < C; ++r) t += *cluster.map_shared_rank(&slots[buf], r);
   }
-#pragma unroll
-  for (int j = 0; j < NV; ++j) v[j] = t[j];
   buf ^= 1;
+  return t;
 }
 
 __device__ __forceinline__ void cluster_barrier(const cg::cluster_group& cluster) {
-  __threadfence();
+  asm volatile("fence.acq_rel.cluster;" ::: "memory");
   cluster.sync();
 }
+
+// CG state of the lattice a cluster is solving: updated by thread 0 of each CTA (identically in
+// every CTA of the cluster), read by the other threads after a __syncthreads.
+struct BatchState {
+  double rr, rr_prev, rmax2, pp, alpha, beta, bb, delit, res2;
+  int iter, since_ru, ru_count, status, action;
+};
+enum { kActRun = 0, kActReliable = 1, kActStop = 2 };
 
 template <int PREC, int RECON>
 __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchItem* __restrict__ items,
@@ -91,18 +95,21 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
   constexpr int XP = x_prec(PREC);
   using XFieldT = Field<XP>;
   using TX = typename XFieldT::T;
+  using A = typename Accum<T>::type;
   constexpr bool mixed = PREC != QCD_PREC_DOUBLE;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int nthreads = (int)cluster.num_blocks() * blockDim.x;
   const int tid = crank * blockDim.x + threadIdx.x;
-  __shared__ double slots[2][4];
+  const bool lead = threadIdx.x == 0;
+  __shared__ double slots[2];
   __shared__ int item_slot;
+  __shared__ BatchState S;
   int buf = 0;
 
   while (true) {
-    if (crank == 0 && threadIdx.x == 0) item_slot = (int)atomicAdd(queue, 1u);
+    if (crank == 0 && lead) item_slot = (int)atomicAdd(queue, 1u);
     cluster.sync();
     const int it = *cluster.map_shared_rank(&item_slot, 0);
     cluster.sync();  // rank 0 may overwrite item_slot only after everyone has read it
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
         x_hi{make_field<QCD_PREC_DOUBLE>(I.x_hi, Vh)}, tmp{make_field<QCD_PREC_DOUBLE>(I.tmp, Vh)};
 
     // ---- start-up: b_hi = b_e, r = b_e, p = 0, x = 0
-    double red[1] = {0.0};
+    double part64 = 0.0;
     for (int k = tid; k < Vh; k += nthreads) {
       const Site s = site_of(g, k, QCD_EVEN);
       cvec3<double> bv;
@@ -143,74 +150,103 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
         zero(zd);
         x_hi.store(k, zd);
       }
-      red[0] += norm2(bv);
+      part64 += norm2(bv);
     }
-    cluster_sum<1>(red, slots, buf, cluster);
-    const double bb = red[0];
-    double rr = bb, rr_prev = bb, rmax2 = bb, pp = 0.0, alpha = 0.0, beta = 0.0;
-    const double delit = I.tol2 * bb;
-    int iter = 0, since_ru = 0, ru_count = 0;
-    int status = isfinite(bb) ? kBatchOk : kBatchBreakdown;
-    bool running = status == kBatchOk && bb > 0.0;
+    {
+      const double bb = cluster_total(part64, slots, buf, cluster);
+      if (lead) {
+        S.bb = S.rr = S.rr_prev = S.rmax2 = bb;
+        S.pp = S.alpha = S.beta = 0.0;
+        S.delit = I.tol2 * bb;
+        S.iter = S.since_ru = S.ru_count = 0;
+        S.status = isfinite(bb) ? kBatchOk : kBatchBreakdown;
+        S.action = (S.status == kBatchOk && bb > 0.0) ? kActRun : kActStop;
+      }
+      __syncthreads();
+    }
 
-    while (running) {
-      // K3: p = r + beta p
-      red[0] = 0.0;
-      for (int k = tid; k < Vh; k += nthreads) {
-        cvec3<T> rv = r.load(k), pv = p.load(k);
+    while (S.action != kActStop) {
+      if (S.action == kActRun) {
+        // K3: p = r + beta p
+        const T beta = (T)S.beta;
+        A part = 0;
+        for (int k = tid; k < Vh; k += nthreads) {
+          cvec3<T> rv = r.load(k), pv = p.load(k);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          pv.c[a].re = fma((T)beta, pv.c[a].re, rv.c[a].re);
-          pv.c[a].im = fma((T)beta, pv.c[a].im, rv.c[a].im);
+          for (int a = 0; a < 3; ++a) {
+            pv.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
+            pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
+          }
+          p.store(k, pv);
+          accum(part, norm2(pv));
         }
-        p.store(k, pv);
-        red[0] += (double)norm2(pv);
-      }
-      cluster_sum<1>(red, slots, buf, cluster);
-      pp = red[0];
-      // K1: ap = D_oe p
-      red[0] = 0.0;
-      for (int k = tid; k < Vh; k += nthreads) {
-        const auto acc = hop(g, U, p, QCD_ODD, k);
-        ap.store(k, acc);
-        red[0] += (double)norm2(acc);
-      }
-      cluster_sum<1>(red, slots, buf, cluster);
-      const double d = red[0] + m2 * pp;
-      alpha = rr / d;
-      if (!(isfinite(d) && d > 0.0) || !isfinite(alpha)) { status = kBatchBreakdown; break; }
-      // K2: x += alpha p; r -= alpha (m^2 p - D_eo ap)
-      red[0] = 0.0;
-      for (int k = tid; k < Vh; k += nthreads) {
-        const auto acc = hop(g, U, ap, QCD_EVEN, k);
-        const cvec3<T> pv = p.load(k);
-        cvec3<T> rv = r.load(k);
-        cvec3<TX> xv = x.load(k);
+        const double pp = cluster_total((double)part, slots, buf, cluster);
+        // K1: ap = D_oe p
+        part = 0;
+        for (int k = tid; k < Vh; k += nthreads) {
+          const auto acc = hop(g, U, p, QCD_ODD, k);
+          ap.store(k, acc);
+          accum(part, norm2(acc));
+        }
+        const double apap = cluster_total((double)part, slots, buf, cluster);
+        if (lead) {
+          const double d = apap + m2 * pp;
+          const double alpha = S.rr / d;
+          if (!(isfinite(d) && d > 0.0) || !isfinite(alpha)) {
+            S.status = kBatchBreakdown;
+            S.action = kActStop;
+          } else {
+            S.alpha = alpha;
+          }
+        }
+        __syncthreads();
+        if (S.action == kActStop) break;
+        // K2: x += alpha p; r -= alpha (m^2 p - D_eo ap)
+        const T alpha = (T)S.alpha;
+        part = 0;
+        for (int k = tid; k < Vh; k += nthreads) {
+          const auto acc = hop(g, U, ap, QCD_EVEN, k);
+          const cvec3<T> pv = p.load(k);
+          cvec3<T> rv = r.load(k);
+          cvec3<TX> xv = x.load(k);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const T at_re = fma((T)m2, pv.c[a].re, -acc.c[a].re);
-          const T at_im = fma((T)m2, pv.c[a].im, -acc.c[a].im);
-          rv.c[a].re = fma(-(T)alpha, at_re, rv.c[a].re);
-          rv.c[a].im = fma(-(T)alpha, at_im, rv.c[a].im);
-          xv.c[a].re = fma((TX)alpha, (TX)pv.c[a].re, xv.c[a].re);
-          xv.c[a].im = fma((TX)alpha, (TX)pv.c[a].im, xv.c[a].im);
+          for (int a = 0; a < 3; ++a) {
+            const T at_re = fma((T)m2, pv.c[a].re, -acc.c[a].re);
+            const T at_im = fma((T)m2, pv.c[a].im, -acc.c[a].im);
+            rv.c[a].re = fma(-alpha, at_re, rv.c[a].re);
+            rv.c[a].im = fma(-alpha, at_im, rv.c[a].im);
+            xv.c[a].re = fma((TX)alpha, (TX)pv.c[a].re, xv.c[a].re);
+            xv.c[a].im = fma((TX)alpha, (TX)pv.c[a].im, xv.c[a].im);
+          }
+          r.store(k, rv);
+          x.store(k, xv);
+          accum(part, norm2(rv));
         }
-        r.store(k, rv);
-        x.store(k, xv);
-        red[0] += (double)norm2(rv);
-      }
-      cluster_sum<1>(red, slots, buf, cluster);
-      iter += 1;
-      since_ru += 1;
-      rr_prev = rr;
-      rr = red[0];
-      if (!isfinite(rr)) { status = kBatchBreakdown; break; }
-      beta = rr / rr_prev;
-      rmax2 = fmax(rmax2, rr);
-      const bool met = rr < delit;
-      // reliable update (mixed: periodic / delta test; both: to confirm convergence on the true
-      // residual): x_hi += x_lo, x_lo = 0; r = b - A x_hi in FP64; r_lo <- r
-      if (met || (mixed && (since_ru >= ru_interval || rr < delta2 * rmax2))) {
+        const double rr = cluster_total((double)part, slots, buf, cluster);
+        if (lead) {
+          S.iter += 1;
+          S.since_ru += 1;
+          S.rr_prev = S.rr;
+          S.rr = rr;
+          if (!isfinite(rr)) {
+            S.status = kBatchBreakdown;
+            S.action = kActStop;
+          } else {
+            S.beta = rr / S.rr_prev;
+            S.rmax2 = fmax(S.rmax2, rr);
+            // reliable update (mixed: periodic / delta test; both: to confirm convergence on the
+            // true residual)
+            if (rr < S.delit || (mixed && (S.since_ru >= ru_interval || rr < delta2 * S.rmax2)))
+              S.action = kActReliable;
+            else if (S.iter >= I.max_iter) {
+              S.status = kBatchMaxIter;
+              S.action = kActStop;
+            }
+          }
+        }
+        __syncthreads();
+      } else {
+        // reliable update: x_hi += x_lo, x_lo = 0; r = b - A x_hi in FP64; r_lo <- r
         if (mixed) {
           for (int k = tid; k < Vh; k += nthreads) {
             cvec3<double> xh = x_hi.load(k);
@@ -226,7 +262,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
         cluster_barrier(cluster);
         for (int k = tid; k < Vh; k += nthreads) tmp.store(k, hop(g, U64, x_hi, QCD_ODD, k));
         cluster_barrier(cluster);
-        red[0] = 0.0;
+        part64 = 0.0;
         for (int k = tid; k < Vh; k += nthreads) {
           const auto acc = hop(g, U64, tmp, QCD_EVEN, k);
           const cvec3<double> bv = b_hi.load(k), xv = x_hi.load(k);
@@ -240,19 +276,31 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
             rl.c[a].im = (T)rv.c[a].im;
           }
           r.store(k, rl);
-          red[0] += norm2(rv);
+          part64 += norm2(rv);
         }
-        cluster_sum<1>(red, slots, buf, cluster);
-        const double rt = red[0];
-        if (!isfinite(rt)) { status = kBatchBreakdown; break; }
-        beta = rt / rr_prev;
-        rr = rt;
-        rmax2 = rt;
-        since_ru = 0;
-        ru_count += 1;
-        if (rt < delit) break;
+        const double rt = cluster_total(part64, slots, buf, cluster);
+        if (lead) {
+          if (!isfinite(rt)) {
+            S.status = kBatchBreakdown;
+            S.action = kActStop;
+          } else {
+            S.beta = rt / S.rr_prev;
+            S.rr = rt;
+            S.rmax2 = rt;
+            S.since_ru = 0;
+            S.ru_count += 1;
+            if (rt < S.delit) {
+              S.action = kActStop;
+            } else if (S.iter >= I.max_iter) {
+              S.status = kBatchMaxIter;
+              S.action = kActStop;
+            } else {
+              S.action = kActRun;
+            }
+          }
+        }
+        __syncthreads();
       }
-      if (iter >= I.max_iter) { status = kBatchMaxIter; break; }
     }
 
     // ---- finish: fold x_lo into x_hi, y = D_oe x, true residual, canonical outputs
@@ -271,7 +319,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
     cluster_barrier(cluster);
     for (int k = tid; k < Vh; k += nthreads) tmp.store(k, hop(g, U64, x_hi, QCD_ODD, k));
     cluster_barrier(cluster);
-    red[0] = 0.0;
+    part64 = 0.0;
     for (int k = tid; k < Vh; k += nthreads) {
       const auto acc = hop(g, U64, tmp, QCD_EVEN, k);
       const cvec3<double> bv = b_hi.load(k), xv = x_hi.load(k), yv = tmp.load(k);
@@ -281,7 +329,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
         rv.c[a].re = bv.c[a].re - fma(m2, xv.c[a].re, -acc.c[a].re);
         rv.c[a].im = bv.c[a].im - fma(m2, xv.c[a].im, -acc.c[a].im);
       }
-      red[0] += norm2(rv);
+      part64 += norm2(rv);
       const Site se = site_of(g, k, QCD_EVEN), so = site_of(g, k, QCD_ODD);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -293,18 +341,19 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
         }
       }
     }
-    cluster_sum<1>(red, slots, buf, cluster);
-    if (crank == 0 && threadIdx.x == 0) {
+    const double res2 = cluster_total(part64, slots, buf, cluster);
+    if (crank == 0 && lead) {
       BatchResult res;
-      res.iterations = iter;
-      res.ru_count = ru_count;
-      res.status = status;
+      res.iterations = S.iter;
+      res.ru_count = S.ru_count;
+      res.status = S.status;
       res.pad = 0;
-      res.bb = bb;
-      res.rr = rr;
-      res.res2 = red[0];
+      res.bb = S.bb;
+      res.rr = S.rr;
+      res.res2 = res2;
       results[it] = res;
     }
+    __syncthreads();  // S is rewritten for the next lattice only after every thread is past it
   }
 }
 

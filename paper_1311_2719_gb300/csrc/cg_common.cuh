@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kBlock) cg_p_kernel(int Vh, FieldT r, FieldT p
   using T = typename FieldT::T;
   if (sc->done != kRunning) return;
   const T beta = (T)sc->beta;
-  double red[1] = {0.0};
+  typename Accum<T>::type part = 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Vh; k += gridDim.x * blockDim.x) {
     cvec3<T> rv = r.load(k), pv = p.load(k);
 #pragma unroll
@@ -91,8 +91,9 @@ __global__ void __launch_bounds__(kBlock) cg_p_kernel(int Vh, FieldT r, FieldT p
       pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
     }
     p.store(k, pv);
-    red[0] += (double)norm2(pv);
+    accum(part, norm2(pv));
   }
+  double red[1] = {(double)part};
   double tot[1];
   if (grid_sum_last_block<1>(red, partials, &sc->counter[1], tot) && threadIdx.x == 0) sc->pp = tot[0];
 }
@@ -106,13 +107,14 @@ struct EpiAp {
   CgScalars* sc;
   double* partials;
   __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
-  template <class T>
-  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double* red) const {
+  template <class T, class A>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, A* red) const {
     ap.store(k, acc);
-    red[0] += (double)norm2(acc);
+    accum(red[0], norm2(acc));
   }
-  __device__ __forceinline__ void finish(double* red) const {
-    double v[1] = {red[0]}, tot[1];
+  template <class A>
+  __device__ __forceinline__ void finish(A* red) const {
+    double v[1] = {(double)red[0]}, tot[1];
     if (grid_sum_last_block<1>(v, partials, &sc->counter[2], tot) && threadIdx.x == 0) {
       const double d = tot[0] + sc->m2 * sc->pp;  // <p, A p> = |D_oe p|^2 + m^2 |p|^2
       const double alpha = sc->rr / d;
@@ -140,10 +142,10 @@ struct EpiUpdate {
   };
   __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
   __device__ __forceinline__ Pre prefetch(int k) const { return Pre{p.load(k), r.load(k), x.load(k)}; }
-  template <class T>
-  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double* red) const { site_pre(k, acc, red, prefetch(k)); }
-  template <class T>
-  __device__ __forceinline__ void site_pre(int k, cvec3<T>& acc, double* red, const Pre& pre) const {
+  template <class T, class A>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, A* red) const { site_pre(k, acc, red, prefetch(k)); }
+  template <class T, class A>
+  __device__ __forceinline__ void site_pre(int k, cvec3<T>& acc, A* red, const Pre& pre) const {
     using TX = typename XFieldT::T;
     const T alpha = (T)sc->alpha, m2 = (T)sc->m2;
     const cvec3<T>& pv = pre.p;
@@ -160,10 +162,11 @@ struct EpiUpdate {
     }
     r.store(k, rv);
     x.store(k, xv);
-    red[0] += (double)norm2(rv);
+    accum(red[0], norm2(rv));
   }
-  __device__ __forceinline__ void finish(double* red) const {
-    double v[1] = {red[0]}, tot[1];
+  template <class A>
+  __device__ __forceinline__ void finish(A* red) const {
+    double v[1] = {(double)red[0]}, tot[1];
     if (grid_sum_last_block<1>(v, partials, &sc->counter[3], tot) && threadIdx.x == 0) {
       const double rr = tot[0];
       sc->iter += 1;
@@ -269,9 +272,10 @@ struct Gated {
   Epi epi;
   const CgScalars* gate;
   __device__ __forceinline__ bool skip() const { return !ru_wanted(gate) || epi.skip(); }
-  template <class T>
-  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double* red) const { epi.site(k, acc, red); }
-  __device__ __forceinline__ void finish(double* red) const { epi.finish(red); }
+  template <class T, class A>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, A* red) const { epi.site(k, acc, red); }
+  template <class A>
+  __device__ __forceinline__ void finish(A* red) const { epi.finish(red); }
 };
 
 // Last node of the device-side solve loop: keep looping while the recursion runs (bounded by

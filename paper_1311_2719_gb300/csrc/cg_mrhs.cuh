@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kBlock) cg_p_mrhs_kernel(int Vh, FieldT r_all,
                                                            double* partials) {
   using T = typename FieldT::T;
   const int r = blockIdx.y;
-  double red[1] = {0.0};
+  typename Accum<T>::type part = 0;
   if (sc[r].done == kRunning) {
     const FieldT rf = field_at(r_all, r), pf = field_at(p_all, r);
     const T beta = (T)sc[r].beta;
@@ -71,9 +71,10 @@ __global__ void __launch_bounds__(kBlock) cg_p_mrhs_kernel(int Vh, FieldT r_all,
         pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
       }
       pf.store(k, pv);
-      red[0] += (double)norm2(pv);
+      accum(part, norm2(pv));
     }
   }
+  double red[1] = {(double)part};
   if (mrhs_arrive<1>(red, r, nrhs, partials, &sc[0].counter[kCtrK3M])) {
     __shared__ double tot[kMaxRhs];
     mrhs_totals(nrhs, partials, tot);
@@ -95,9 +96,10 @@ __global__ void __launch_bounds__(kBlock) dslash_mrhs_cg_kernel(Geom g, LinksT U
 #pragma unroll
   for (int j = 0; j < RB; ++j)
     if (r0 + j < nrhs && epi.sc[r0 + j].done == kRunning) active |= 1u << j;
-  double red[RB];
+  using A = typename Accum<T>::type;
+  A part[RB];
 #pragma unroll
-  for (int j = 0; j < RB; ++j) red[j] = 0.0;
+  for (int j = 0; j < RB; ++j) part[j] = A(0);
   if (active) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
       const Site s = site_of(g, k, out_par);
@@ -121,9 +123,12 @@ __global__ void __launch_bounds__(kBlock) dslash_mrhs_cg_kernel(Geom g, LinksT U
       }
 #pragma unroll
       for (int j = 0; j < RB; ++j)
-        if ((active >> j) & 1u) epi.site(k, r0 + j, acc[j], red[j]);
+        if ((active >> j) & 1u) epi.site(k, r0 + j, acc[j], part[j]);
     }
   }
+  double red[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) red[j] = (double)part[j];
   if (mrhs_arrive<RB>(red, r0, nrhs, epi.partials, &epi.sc[0].counter[Epi::kCounter])) {
     __shared__ double tot[kMaxRhs];
     mrhs_totals(nrhs, epi.partials, tot);
@@ -142,10 +147,10 @@ struct EpiApM {
   FieldT ap;
   CgScalars* sc;
   double* partials;
-  template <class T>
-  __device__ __forceinline__ void site(int k, int r, const cvec3<T>& acc, double& red) const {
+  template <class T, class A>
+  __device__ __forceinline__ void site(int k, int r, const cvec3<T>& acc, A& red) const {
     field_at(ap, r).store(k, acc);
-    red += (double)norm2(acc);
+    accum(red, norm2(acc));
   }
   __device__ __forceinline__ void update(int r, double apap) const {
     CgScalars& s = sc[r];
@@ -164,8 +169,8 @@ struct EpiUpdateM {
   XFieldT x;
   CgScalars* sc;
   double* partials;
-  template <class T>
-  __device__ __forceinline__ void site(int k, int q, const cvec3<T>& acc, double& red) const {
+  template <class T, class A>
+  __device__ __forceinline__ void site(int k, int q, const cvec3<T>& acc, A& red) const {
     using TX = typename XFieldT::T;
     const T alpha = (T)sc[q].alpha, m2 = (T)sc[q].m2;
     const FieldT pf = field_at(p, q), rf = field_at(r, q);
@@ -184,7 +189,7 @@ struct EpiUpdateM {
     }
     rf.store(k, rv);
     xf.store(k, xv);
-    red += (double)norm2(rv);
+    accum(red, norm2(rv));
   }
   __device__ __forceinline__ void update(int q, double rr) const {
     CgScalars& s = sc[q];
@@ -260,9 +265,12 @@ struct MrhsRunner {
   }
 };
 
-// Largest RHS block that keeps the register-resident accumulators within budget.
+// Default RHS block (when nothing is tuned): at most 4. Measured on GB300, 16 right-hand sides
+// in registers take 254 registers per thread, leave 2 blocks per SM and run at a tenth of the
+// memory bandwidth; qcd_tune_mrhs can still choose 8 or 16 where they pay.
 inline int default_rhs_block(int prec, int R) {
-  const int cap = (prec == QCD_PREC_DOUBLE || prec == QCD_PREC_DF64) ? 4 : 16;
+  const int cap = 4;
+  (void)prec;
   int rb = 1;
   while (rb * 2 <= R && rb * 2 <= cap) rb *= 2;
   if (rb < R && rb * 2 <= cap) rb *= 2;  // one partially filled block beats two passes

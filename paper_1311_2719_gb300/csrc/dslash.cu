@@ -12,8 +12,8 @@ struct EpiMdagm {
   FieldT in, out;
   double m2;
   __device__ __forceinline__ bool skip() const { return false; }
-  template <class T>
-  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double*) const {
+  template <class T, class A>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, A*) const {
     cvec3<T> v = in.load(k);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -22,7 +22,8 @@ struct EpiMdagm {
     }
     out.store(k, v);
   }
-  __device__ __forceinline__ void finish(double*) const {}
+  template <class A>
+  __device__ __forceinline__ void finish(A*) const {}
 };
 
 template <int PREC, int RECON>

@@ -96,8 +96,8 @@ __device__ __forceinline__ void pair_sum(cvec3<T>& acc) {
 //   static constexpr bool kPrefetch;                true: prefetch(k) / site_pre(k, acc, red, pre)
 //                                                   are used on the one-thread-per-site path
 //   bool skip() const;                              true -> whole kernel returns at once
-//   void site(int k, cvec3<T>& acc, double* red);   consume the hop result of site k
-//   void finish(double* red);                       grid reduction + scalar update (NV > 0)
+//   void site(int k, cvec3<T>& acc, A* red);        consume the hop result of site k (A = Accum<T>)
+//   void finish(A* red);                            grid reduction + scalar update (NV > 0)
 // TPS = threads per output site: 1, or 2 (forward / backward hops on a lane pair, for lattices
 // too small to fill the GPU with one thread per site).
 // Resident blocks per SM the operator kernels are compiled for: 8 (<= 64 registers) for the
@@ -114,9 +114,10 @@ template <class LinksT, class FieldT, class Epi, int TPS = 1>
 __global__ void __launch_bounds__(kBlock, MinBlocks<LinksT>::value) dslash_kernel(Geom g, LinksT U, FieldT in,
                                                                                  int out_par, Epi epi) {
   if (epi.skip()) return;
-  double red[Epi::NV > 0 ? Epi::NV : 1];
+  using A = typename Accum<typename LinksT::T>::type;
+  A red[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
-  for (int j = 0; j < (Epi::NV > 0 ? Epi::NV : 1); ++j) red[j] = 0.0;
+  for (int j = 0; j < (Epi::NV > 0 ? Epi::NV : 1); ++j) red[j] = A(0);
   if constexpr (TPS == 1) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
       if constexpr (Epi::kPrefetch) {
@@ -154,11 +155,12 @@ struct EpiStore {
   static constexpr bool kPrefetch = false;
   FieldT out;
   __device__ __forceinline__ bool skip() const { return false; }
-  template <class T>
-  __device__ __forceinline__ void site(int k, cvec3<T>& acc, double*) const {
+  template <class T, class A>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, A*) const {
     out.store(k, acc);
   }
-  __device__ __forceinline__ void finish(double*) const {}
+  template <class A>
+  __device__ __forceinline__ void finish(A*) const {}
 };
 
 template <int PREC>

@@ -506,6 +506,22 @@ inline size_t links_bytes(int prec, int recon, long long Vh) {
   return 0;
 }
 
+// Per-thread partial sums of the norms: FP32 in FP32-arithmetic kernels (a thread adds a few
+// sites' values; converted to FP64 once, at the block sum), FP64 otherwise. Keeps the FP64
+// pipe, 1/64 of the FP32 rate on GB300, out of the per-site work.
+template <class T>
+struct Accum {
+  using type = double;
+};
+template <>
+struct Accum<float> {
+  using type = float;
+};
+__device__ __forceinline__ void accum(float& r, float v) { r += v; }
+__device__ __forceinline__ void accum(double& r, double v) { r += v; }
+__device__ __forceinline__ void accum(double& r, float v) { r += (double)v; }
+__device__ __forceinline__ void accum(double& r, df64 v) { r += (double)v; }
+
 // ------------------------------------------------------------------------------------------
 // Deterministic reductions: per-block partial sums in FP64, the last block to finish sums the
 // partials in a fixed order (so results do not depend on block scheduling).
