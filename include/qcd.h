@@ -239,6 +239,15 @@ QCD_API int qcd_cg_solve_batched(int n, qcd_lattice* const lats[], void* const x
                          void* const y[], const double mass[], double tol, int max_iter,
                          const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info info[], void* stream);
 
+/* Full-system solve M x = b with M = m + D on both parities (b, x: device canonical fields
+ * complex128[V][3]), by even-odd reduction onto qcd_cg_solve: (m^2 - D_eo D_oe) x_e = m b_e - D_eo b_o,
+ * then x_o = (b_o - D_oe x_e) / m. The even system is solved to tol * m |b| / |b_e'| so that the full
+ * FP64 residual |b - M x| / |b|, recomputed at the end and returned in info->true_rel_residual,
+ * meets tol. workspace_dev: qcd_workspace_bytes_full(lat, opts) bytes. Synchronises `stream`. */
+QCD_API size_t qcd_workspace_bytes_full(const qcd_lattice* lat, const qcd_solver_opts* opts);
+QCD_API int qcd_solve_full(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, double tol, int max_iter,
+                   const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream);
+
 /* ---- autotuning of launch shapes (no counterpart in the paper) ------------------------------ */
 
 /* Time the multi-RHS solver's operator launches (CUDA events over a 24-iteration run of the real

@@ -296,3 +296,41 @@ def neighbour_tables_of_sites(dims, sites):
         iup[:, mu] = sites + (((c + 1) % L[mu]) - c) * stride[mu]
         idn[:, mu] = sites + (((c - 1) % L[mu]) - c) * stride[mu]
     return iup, idn
+
+
+def apply_m(U, x, dims, mass: float, tbc: float = -1.0) -> np.ndarray:
+    """The full staggered operator M x = m x + D x on both parities."""
+    return mass * np.asarray(x, np.complex128) + dslash(U, x, dims, tbc)
+
+
+def solve_full(U, b, dims, mass: float, tol: float, max_iter: int, tbc: float = -1.0):
+    """x = M^-1 b on the full lattice, M = m + D.
+
+    Textbook CG on the normal equations M^dagger M x = M^dagger b, with M^dagger = m - D (D is
+    anti-Hermitian) and M^dagger M = m^2 - D^2, over both parities at once; no even-odd
+    reduction. Stops when |M^dagger b - M^dagger M x| <= tol |M^dagger b|.
+    Returns dict(x, iterations, rel_residual = |b - M x| / |b|).
+    """
+    b = np.asarray(b, np.complex128)
+    rhs = mass * b - dslash(U, b, dims, tbc)
+
+    def normal(v):
+        return mass * mass * v - dslash(U, dslash(U, v, dims, tbc), dims, tbc)
+
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    p = r.copy()
+    rr = _norm2(r)
+    stop = tol * tol * _norm2(rhs)
+    it = 0
+    while rr > stop and it < max_iter:
+        ap = normal(p)
+        alpha = rr / float(np.vdot(p.reshape(-1), ap.reshape(-1)).real)
+        x = x + alpha * p
+        r = r - alpha * ap
+        rr_new = _norm2(r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    res = b - apply_m(U, x, dims, mass, tbc)
+    return {"x": x, "iterations": it, "rel_residual": float(np.sqrt(_norm2(res) / _norm2(b)))}

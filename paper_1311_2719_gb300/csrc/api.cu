@@ -35,6 +35,9 @@ size_t cg_workspace_bytes(const qcd_lattice*, int, int);
 int run_cg(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*,
            qcd_solve_info*, cudaStream_t);
 size_t batch_workspace_bytes(int, const qcd_lattice* const*, int);
+size_t full_workspace_bytes(const qcd_lattice*, int);
+int run_solve_full(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*,
+                   qcd_solve_info*, cudaStream_t);
 int run_cg_batched(int, qcd_lattice* const*, void* const*, const void* const*, void* const*, const double*, double, int,
                    const qcd_solver_opts&, void*, qcd_solve_info*, cudaStream_t);
 int run_cg_mrhs(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*,
@@ -367,6 +370,31 @@ int qcd_cg_solve_batched(int n, qcd_lattice* const lats[], void* const x[], cons
       return done(invalid("every lattice must load the inner links with the same reconstruction"));
   }
   return done(run_cg_batched(n, lats, x, b, y, mass, tol, max_iter, o, workspace_dev, info, as_stream(stream)));
+}
+
+size_t qcd_workspace_bytes_full(const qcd_lattice* lat, const qcd_solver_opts* opts) {
+  if (!lat) return 0;
+  qcd_solver_opts o;
+  qcd_solver_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_prec(o.prec_inner)) return 0;
+  return full_workspace_bytes(lat, o.prec_inner);
+}
+
+int qcd_solve_full(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, double tol, int max_iter,
+                   const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (info) std::memset(info, 0, sizeof(*info));
+  auto done = [&](int rc) {
+    if (info) {
+      info->status = rc;
+      info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return rc;
+  };
+  qcd_solver_opts o;
+  if (int rc = check_solve_args(lat, x_dev, b_dev, workspace_dev, nullptr, mass, tol, max_iter, opts, o)) return done(rc);
+  return done(run_solve_full(lat, x_dev, b_dev, mass, tol, max_iter, o, workspace_dev, info, as_stream(stream)));
 }
 
 }  // extern "C"

@@ -53,6 +53,18 @@ __device__ __forceinline__ void mrhs_totals(int nrhs, const double* partials, do
   __syncthreads();
 }
 
+// Last node of the device-side multi-RHS loop: loop again while any right-hand side still runs.
+static __global__ void mrhs_loop_control_kernel(CgScalars* sc, int nrhs, cudaGraphConditionalHandle handle,
+                                                int max_loops) {
+  const int lane = threadIdx.x;
+  const bool running = lane < nrhs && sc[lane].done == kRunning;
+  const unsigned any = __ballot_sync(0xffffffffu, running);
+  if (lane == 0) {
+    const int loops = ++sc[0].loops;
+    cudaGraphSetConditional(handle, (any != 0u && loops < max_loops) ? 1u : 0u);
+  }
+}
+
 // ---------------------------------------------------------------- K3: p_r = r_r + beta_r p_r
 template <class FieldT>
 __global__ void __launch_bounds__(kBlock) cg_p_mrhs_kernel(int Vh, FieldT r_all, FieldT p_all, int nrhs, CgScalars* sc,
@@ -222,9 +234,25 @@ struct MrhsRunner {
   int grid, R, rb;
   long long launches = 0;
 
+  // x-extent of a grid with `gy` rows that stays within one wave of resident blocks of `kernel`
+  // (every block ends in a fence + counter update; more waves multiply that cost).
+  template <class KernelT>
+  int wave_x(KernelT kernel, int gy) const {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const long long need = (g.Vh + kBlock - 1) / kBlock;
+    long long gx = (long long)sms * per_sm / gy;
+    if (gx > need) gx = need;
+    if (gx > kMaxPartials) gx = kMaxPartials;
+    return (int)(gx > 0 ? gx : 1);
+  }
+
   template <int RB>
   void launch_ops(const Links<PREC, RECON>& U, FieldT p, FieldT ap, FieldT r, XFieldT x, cudaEvent_t* ev) {
-    const dim3 gr(grid, (R + RB - 1) / RB);
+    const int gy = (R + RB - 1) / RB;
+    const dim3 gr(wave_x(dslash_mrhs_cg_kernel<Links<PREC, RECON>, FieldT, RB, EpiUpdateM<FieldT, XFieldT>>, gy), gy);
     if (ev) cudaEventRecord(ev[0], st);
     dslash_mrhs_cg_kernel<Links<PREC, RECON>, FieldT, RB><<<gr, kBlock, 0, st>>>(
         g, U, p, R, QCD_ODD, EpiApM<FieldT>{ap, w.sc, w.partials});
@@ -239,7 +267,7 @@ struct MrhsRunner {
     auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
     FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh), ap = make_field<PREC>(w.ap, g.Vh);
     XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
-    cg_p_mrhs_kernel<<<dim3(grid, R), kBlock, 0, st>>>(g.Vh, r, p, R, w.sc, w.partials);
+    cg_p_mrhs_kernel<<<dim3(wave_x(cg_p_mrhs_kernel<FieldT>, R), R), kBlock, 0, st>>>(g.Vh, r, p, R, w.sc, w.partials);
     constexpr bool wide = PREC == QCD_PREC_DOUBLE || PREC == QCD_PREC_DF64;  // 64-bit accumulators: RB <= 4
     switch (rb) {
       case 1: launch_ops<1>(U, p, ap, r, x, ev); break;
@@ -332,24 +360,53 @@ int mrhs_typed(qcd_lattice* lat, int R, void* x, const void* b, double mass, dou
     if (ce != cudaSuccess) { cleanup(); return cuda_fail(ce, "cudaEventCreate"); }
   }
   auto ev_at = [&](int i) -> cudaEvent_t* { return profile ? &ev[4 * i] : nullptr; };
+  // With a stream the whole loop is one graph launch: a conditional WHILE node whose body is k
+  // iterations, every RHS's flag-gated reliable update and a control kernel (as in cg.cu).
   const bool use_graph = o.use_graph && st != nullptr && !profile;
   if (use_graph) {
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaStreamBeginCapture"); }
+    QCD_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    QCD_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams params = {};
+    params.type = cudaGraphNodeTypeConditional;
+    params.conditional.handle = handle;
+    params.conditional.type = cudaGraphCondTypeWhile;
+    params.conditional.size = 1;
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &params);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaGraphAddNode"); }
+    cudaGraph_t body = params.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
     const long long before = M.launches;
     for (int i = 0; i < k && rc == QCD_OK; ++i) rc = M.iteration();
+    for (int r = 0; r < R && rc == QCD_OK; ++r) {
+      auto c = M.single(r);
+      rc = c.reliable_update(true);
+    }
+    const int max_loops = max_iter / k + 2 * (max_iter / 100 + 1) + 16;
+    if (rc == QCD_OK) mrhs_loop_control_kernel<<<1, 32, 0, st>>>(M.w.sc, R, handle, max_loops);
     M.launches = before;
-    e = cudaStreamEndCapture(st, &graph);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(st, &captured);
     if (rc) { cleanup(); return rc; }
     if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaStreamEndCapture"); }
     e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaGraphInstantiate"); }
+    e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaGraphLaunch"); }
   }
 
   int dslash_launches = 0;
   double dslash_ms = 0.0;
   if ((rc = read_scalars(M.w, h.data(), st, R))) { cleanup(); return rc; }
-  while (true) {
+  if (use_graph) {
+    int it_max = 0;
+    for (int r = 0; r < R; ++r) it_max = std::max(it_max, h[r].iter);
+    dslash_launches = 2 * it_max;
+    M.launches += (long long)h[0].loops * (3ll * k + (mixed ? 3 : 2) * R + 1);
+  }
+  while (!use_graph) {
     bool any_running = false, any_ru = false;
     for (int r = 0; r < R; ++r) {
       const int d = h[r].done;

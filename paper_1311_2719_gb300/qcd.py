@@ -101,6 +101,9 @@ SIGNATURES = {
     "qcd_cg_solve_batched": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                   ctypes.POINTER(_vp), ctypes.POINTER(_d), _d, _i, ctypes.POINTER(qcd_solver_opts),
                                   _vp, ctypes.POINTER(qcd_solve_info), _vp]),
+    "qcd_workspace_bytes_full": (_sz, [_vp, ctypes.POINTER(qcd_solver_opts)]),
+    "qcd_solve_full": (_i, [_vp, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp,
+                            ctypes.POINTER(qcd_solve_info), _vp]),
     "qcd_tune_mrhs": (_i, [_vp, _i, _vp, _vp, _d, ctypes.POINTER(qcd_solver_opts), _vp, ctypes.c_char_p,
                            ctypes.POINTER(_i), _vp]),
     "qcd_tune_batched": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
@@ -278,6 +281,22 @@ def qcd_cg_solve_batched(lats, x_devs, b_devs, y_devs, masses, tol, max_iter, op
     if rc in raise_on:
         _check(rc, "qcd_cg_solve_batched")
     return rc, [infos[i].as_dict() for i in range(n)]
+
+
+def qcd_workspace_bytes_full(lat, opts=None) -> int:
+    return _lib.qcd_workspace_bytes_full(lat, ctypes.byref(opts) if opts is not None else None)
+
+
+def qcd_solve_full(lat, x_dev, b_dev, mass, tol, max_iter, opts, workspace_dev, stream=None,
+                   raise_on=(QCD_ERR_INVALID_ARG, QCD_ERR_CUDA, QCD_ERR_UNSUPPORTED, QCD_ERR_NO_LINKS)):
+    """x = M^-1 b on both parities. Returns (status, info dict)."""
+    info = qcd_solve_info()
+    rc = _lib.qcd_solve_full(lat, _ptr(x_dev), _ptr(b_dev), float(mass), float(tol), int(max_iter),
+                             ctypes.byref(opts) if opts is not None else None, _ptr(workspace_dev),
+                             ctypes.byref(info), _stream(stream))
+    if rc in raise_on:
+        _check(rc, "qcd_solve_full")
+    return rc, info.as_dict()
 
 
 def qcd_tune_mrhs(lat, nrhs, x_dev, b_dev, mass, opts, workspace_dev, cache_path=None, stream=None) -> int:

@@ -73,14 +73,20 @@ def test_mrhs_fp64_agrees_with_single_rhs_solves(H):
             assert H.rel(x[r], x1) <= 1e-9, (rb, r)
 
 
-def test_mrhs_result_does_not_depend_on_rhs_block(H):
+def test_mrhs_results_agree_across_rhs_blocks(H):
+    """Every register block solves the same systems; the grid (and so the reduction order) differs
+    with the block, so the solutions agree to the solve's own accuracy (kappa * tol), and a
+    repeated run with the same block is bit-identical."""
     dims, m = (4, 4, 6, 8), 0.05
     U = I.make_links(dims, kind="haar", seed=3)
     bs = list(I.make_sources(dims, 5, first_seed=7))
     rig = H.Rig(dims, U, precs=["double", "single12"])
     outs = [_mrhs(H, rig, bs, m, "single12", rb=rb)[2] for rb in (1, 2, 4, 8, 16)]
     for o in outs[1:]:
-        assert np.array_equal(o, outs[0])
+        for r in range(5):
+            assert H.rel(o[r], outs[0][r]) <= _kappa(m) * 2e-10
+    again = _mrhs(H, rig, bs, m, "single12", rb=4)[2]
+    assert np.array_equal(again, outs[2])
 
 
 def test_mrhs_status_per_rhs(H):

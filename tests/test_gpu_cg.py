@@ -148,3 +148,45 @@ def test_df64_cg_full_size_16_4(H):
     # same recursion up to rounding: iteration counts within a few, solutions to ~kappa * tol
     assert abs(info["iterations"] - info64["iterations"]) <= 5
     assert H.rel(x, x64) <= 1e-8
+
+
+def _solve_full(H, rig, b, m, tol=1e-10, inner="double"):
+    import torch
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner, opts.recon_inner = H.PRECS[inner]
+    ws = torch.empty(Q.qcd_workspace_bytes_full(rig.h, opts), dtype=torch.uint8, device="cuda")
+    bd = H.dev(b)
+    x = torch.zeros_like(bd)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    rc, info = Q.qcd_solve_full(rig.h, x, bd, m, tol, 20000, opts, ws, stream=s)
+    s.synchronize()
+    return rc, info, H.host(x)
+
+
+@pytest.mark.parametrize("inner", ["double", "single12", "half12", "df64"])
+@pytest.mark.parametrize("dims,m", [((2, 4, 6, 8), 0.1), ((6, 6, 6, 6), 0.05), ((4, 4, 4, 8), 0.5)])
+def test_full_system_solve_matches_oracle(H, inner, dims, m):
+    """M x = b on both parities (M = m + D): GPU even-odd reduction vs the oracle's full-lattice CG."""
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    rig = H.Rig(dims, U, precs=sorted({"double", inner}))
+    rc, info, x = _solve_full(H, rig, b, m, 1e-10, inner)
+    assert rc == Q.QCD_OK, info
+    assert info["true_rel_residual"] <= 1e-10
+    res = b - S.apply_m(U, x, dims, m)
+    assert np.linalg.norm(res) / np.linalg.norm(b) <= 1.01e-10
+    ref = S.solve_full(U, b, dims, m, tol=1e-13, max_iter=20000)
+    assert H.rel(x, ref["x"]) <= (1.0 + 4.0 / m) * 1e-10 * 10
+
+
+def test_full_system_solve_16_4(H):
+    dims, m = (16, 16, 16, 16), 0.1
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    rig = H.Rig(dims, U, precs=["double", "df64"])
+    for inner in ("double", "df64"):
+        rc, info, x = _solve_full(H, rig, b, m, 1e-10, inner)
+        assert rc == Q.QCD_OK and info["true_rel_residual"] <= 1e-10
+        res = b - S.apply_m(U, x, dims, m)
+        assert np.linalg.norm(res) / np.linalg.norm(b) <= 1.01e-10

@@ -304,3 +304,17 @@ def test_site_local_forms_match_full_lattice_forms(dims):
     iup, idn = S.neighbour_tables(dims)
     a, b = S.neighbour_tables_of_sites(dims, sites)
     assert np.array_equal(a, iup) and np.array_equal(b, idn)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 6, 8)])
+def test_full_system_solve_matches_dense(dims):
+    """x = M^-1 b for M = m + D on the full lattice: CG on M^dagger M vs LAPACK on the dense M."""
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    m = 0.1
+    V = S.volume(dims)
+    M = S.dense_operator(lambda v: S.apply_m(U, v, dims, m), V)
+    x_dense = np.linalg.solve(M, b.reshape(-1)).reshape(-1, 3)
+    res = S.solve_full(U, b, dims, m, tol=1e-13, max_iter=5000)
+    assert res["rel_residual"] <= 1e-11
+    assert _rel(res["x"], x_dense) <= 1e-10
