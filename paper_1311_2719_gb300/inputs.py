@@ -85,6 +85,11 @@ def make_source(dims, seed: int = 2) -> np.ndarray:
     return np.ascontiguousarray(_complex_gaussian(_rng(seed), (volume(dims), 3)))
 
 
+def make_spinor(dims, seed: int = 2) -> np.ndarray:
+    """Complex Gaussian Wilson spinor field complex128[V][4][3] (spin, colour)."""
+    return np.ascontiguousarray(_complex_gaussian(_rng(seed), (volume(dims), 4, 3)))
+
+
 def make_sources(dims, nrhs: int, first_seed: int = 2) -> np.ndarray:
     """nrhs sources with seeds first_seed, first_seed+1, ...; complex128[nrhs][V][3]."""
     return np.stack([make_source(dims, first_seed + k) for k in range(nrhs)])
