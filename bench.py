@@ -55,6 +55,10 @@ WORKLOADS = {
                             inner="single12", nrhs=16,
                             desc="staggered 24^4 Haar, m=0.05, 16 RHS in one multi-RHS CG: FP32 recon-12 inner, "
                                  "FP64 reliable updates"),
+    "wilson32c64_single": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
+                               inner="single18",
+                               desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion with "
+                                    "FP64 reliable updates, to 1e-10"),
     "batch64_single12": dict(kind_solve="batched", n=64, tol=1e-10, inner="single12",
                              desc="64 independent staggered lattices {4^4,6^4,8^4,8^3x16}, m in [0.02,0.5], one "
                                   "persistent clustered CG launch: FP32 recon-12 inner, FP64 reliable updates"),
@@ -499,6 +503,99 @@ def run_gpu_batched(args, wl):
     return out if rank == 0 else None
 
 
+WILSON_FLOP_PER_SITE = 1320
+
+
+def run_gpu_wilson(args, wl):
+    """Wilson CGNR (M = 1 - kappa D_W, full lattice). One step = pack the links at FP64 and FP32 and
+    run the mixed CGNR; value = Wilson Dslash GFLOP/s inside the solve (1320 flop per site per D_W,
+    two D_W per iteration plus the FP64 reliable updates). The plain FP64 CGNR is timed beside."""
+    import torch
+
+    from paper_1311_2719_gb300 import inputs as I
+    from paper_1311_2719_gb300 import qcd as Q
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dims, kappa, tol = wl["dims"], wl["kappa"], wl["tol"]
+    stream = torch.cuda.Stream()
+    lat = Q.Lattice(dims)
+    U_dev = torch.from_numpy(I.make_links(dims, kind=wl["kind"], seed=1)).cuda()
+    b_dev = torch.from_numpy(I.make_spinor(dims, seed=2)).cuda()
+    x_dev = torch.zeros_like(b_dev)
+    bufs = {p: lat.empty_bytes(Q.qcd_wilson_links_bytes(lat.handle, p)) for p in (0, 1)}
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def solve(prec):
+        opts = Q.qcd_solver_opts_default()
+        opts.prec_inner = prec
+        ws = lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts))
+        with torch.cuda.stream(stream):
+            for p, buf in bufs.items():
+                Q.qcd_wilson_load_links(lat.handle, U_dev, buf, p, stream)
+            rc, info = Q.qcd_wilson_cgnr(lat.handle, x_dev, b_dev, kappa, tol, 100000, opts, ws, stream=stream)
+        if rc != Q.QCD_OK:
+            raise RuntimeError(f"Wilson CGNR failed: {Q.qcd_status_string(rc)} {info}")
+        return info
+
+    def timed(prec, n):
+        ms, infos = [], []
+        for _ in range(n):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(solve(prec))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, infos
+
+    for _ in range(args.warmup):
+        solve(1)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    proc, cpath = _clock_sampler(uuid)
+    time.sleep(0.3)
+    ms, infos = timed(1, args.steps)
+    clocks = _clock_summary(proc, cpath)
+    solve(0)
+    ms64, infos64 = timed(0, max(1, min(args.steps, 2)))
+    V = lat.V
+    flops = sum(WILSON_FLOP_PER_SITE * V * (2 * i["iterations"] + 2 * i["reliable_updates"] + 4) for i in infos)
+    tot = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
+    fl = torch.tensor([float(flops)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        dist.all_reduce(fl, op=dist.ReduceOp.SUM)
+    t_mixed, t_64 = sum(ms) / len(ms), sum(ms64) / len(ms64)
+    out = {
+        "metric": METRIC, "value": round(fl.item() / (tot.item() * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_mixed, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 reliable updates)", "data": "synthetic (seeded Haar SU(3) links, Gaussian spinor)",
+        "config": {"workload": wl["desc"], "dims": list(dims), "kappa": kappa, "tol": tol,
+                   "parallelism": f"replicas x{world} (no sharding)",
+                   "l2": "flushed before every step (512 MB write, outside the timed events)",
+                   "step": "qcd_wilson_load_links (FP64 + FP32) + qcd_wilson_cgnr"},
+        "cg": {"iterations": infos[-1]["iterations"], "true_rel_residual": infos[-1]["true_rel_residual"],
+               "reliable_updates": infos[-1]["reliable_updates"], "time_to_solution_ms": round(t_mixed, 4),
+               "plain_fp64_cgnr_ms": round(t_64, 4), "plain_fp64_iterations": infos64[-1]["iterations"],
+               "speedup_vs_plain_fp64_cgnr": round(t_64 / t_mixed, 3)},
+        "gpu_launches": int(sum(i["kernel_launches"] + 2 for i in infos)),
+        "clocks": clocks,
+    }
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
 def _oracle_sample(wl, iters, U=None, b=None):
     """Time the FP64 oracle CG, as it stands, for `iters` iterations of the workload."""
     from oracle import staggered as S
@@ -573,6 +670,8 @@ def main():
         out = run_reference(args, wl)
     elif wl.get("kind_solve") in ("mrhs", "batched"):
         out = run_gpu_batched(args, wl)
+    elif wl.get("kind_solve") == "wilson":
+        out = run_gpu_wilson(args, wl)
     else:
         out = run_gpu(args, wl)
     if out is not None:

@@ -248,6 +248,35 @@ QCD_API size_t qcd_workspace_bytes_full(const qcd_lattice* lat, const qcd_solver
 QCD_API int qcd_solve_full(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, double tol, int max_iter,
                    const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream);
 
+/* ---- Wilson fermions (the paper's second program, §2 and §6) --------------------------------- */
+
+/* Wilson hopping term on the full lattice (no even-odd reduction), DeGrand-Rossi gamma matrices
+ * (mu = x, y, z, t), antiperiodic in t by the handle's tbc:
+ *   D_W psi(n) = sum_mu [ (1 - gamma_mu) U_mu(n) psi(n+mu) + (1 + gamma_mu) U_mu(n-mu)^dagger psi(n-mu) ]
+ *   M = 1 - kappa D_W,  M^dagger = gamma5 M gamma5,  gamma5 = diag(1, 1, -1, -1).
+ * Canonical spinor field: complex128[V][4][3] (spin, colour); packed field: the library's
+ * structure-of-arrays layout over all V sites (qcd_wilson_field_bytes). Precisions: DOUBLE, SINGLE. */
+enum { QCD_WILSON_DSLASH = 0, QCD_WILSON_M = 1, QCD_WILSON_MDAG = 2 };
+QCD_API size_t qcd_wilson_field_bytes(const qcd_lattice* lat, int prec);
+QCD_API size_t qcd_wilson_links_bytes(const qcd_lattice* lat, int prec);
+/* Pack the canonical links for the Wilson operator (the tbc sign folded into the last time slice's
+ * t-links) into packed_dev and register them for `prec`. */
+QCD_API int qcd_wilson_load_links(qcd_lattice* lat, const void* links_dev, void* packed_dev, int prec, void* stream);
+QCD_API int qcd_wilson_pack_field(const qcd_lattice* lat, void* packed_dev, const void* canonical_dev, int prec,
+                          void* stream);
+QCD_API int qcd_wilson_unpack_field(const qcd_lattice* lat, void* canonical_dev, const void* packed_dev, int prec,
+                            void* stream);
+/* out = D_W in (op 0), M in (op 1) or M^dagger in (op 2); packed fields at `prec`, no aliasing.
+ * A spin-projected kernel: each hop multiplies two colour vectors by the link. */
+QCD_API int qcd_wilson_op(const qcd_lattice* lat, void* out_dev, const void* in_dev, double kappa, int op, int prec,
+                  void* stream);
+QCD_API size_t qcd_wilson_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts);
+/* CGNR: M^dagger M x = M^dagger b to |M^dagger b - M^dagger M x| / |M^dagger b| <= tol (recomputed in FP64,
+ * returned in info->true_rel_residual); canonical spinor fields. opts->prec_inner = SINGLE runs the
+ * recursion in FP32 with FP64 reliable updates (links loaded at both precisions). */
+QCD_API int qcd_wilson_cgnr(qcd_lattice* lat, void* x_dev, const void* b_dev, double kappa, double tol, int max_iter,
+                    const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream);
+
 /* ---- autotuning of launch shapes (no counterpart in the paper) ------------------------------ */
 
 /* Time the multi-RHS solver's operator launches (CUDA events over a 24-iteration run of the real

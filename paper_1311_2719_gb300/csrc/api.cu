@@ -35,6 +35,14 @@ size_t cg_workspace_bytes(const qcd_lattice*, int, int);
 int run_cg(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*, void*,
            qcd_solve_info*, cudaStream_t);
 size_t batch_workspace_bytes(int, const qcd_lattice* const*, int);
+size_t wfield_bytes(int, long long);
+size_t wlinks_bytes(int, long long);
+size_t wilson_workspace_bytes(const qcd_lattice*, int);
+int launch_wilson_pack_links(const qcd_lattice*, const void*, void*, int, cudaStream_t);
+int launch_wilson_pack(const qcd_lattice*, void*, const void*, int, bool, cudaStream_t);
+int launch_wilson_op(const qcd_lattice*, void*, const void*, double, int, int, cudaStream_t);
+int run_wilson_cgnr(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*,
+                    qcd_solve_info*, cudaStream_t);
 size_t full_workspace_bytes(const qcd_lattice*, int);
 int run_solve_full(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*,
                    qcd_solve_info*, cudaStream_t);
@@ -130,6 +138,7 @@ int qcd_lattice_set_tbc(qcd_lattice* lat, int sign) {
   if (sign != lat->tbc) {
     lat->tbc = sign;
     for (auto& l : lat->links) l = LinkSet{};
+    lat->wilson_links[0] = lat->wilson_links[1] = nullptr;
   }
   return QCD_OK;
 }
@@ -395,6 +404,98 @@ int qcd_solve_full(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass
   qcd_solver_opts o;
   if (int rc = check_solve_args(lat, x_dev, b_dev, workspace_dev, nullptr, mass, tol, max_iter, opts, o)) return done(rc);
   return done(run_solve_full(lat, x_dev, b_dev, mass, tol, max_iter, o, workspace_dev, info, as_stream(stream)));
+}
+
+static bool wilson_prec(int p) { return p == QCD_PREC_DOUBLE || p == QCD_PREC_SINGLE; }
+
+size_t qcd_wilson_field_bytes(const qcd_lattice* lat, int prec) {
+  return (lat && wilson_prec(prec)) ? wfield_bytes(prec, lat->V) : 0;
+}
+
+size_t qcd_wilson_links_bytes(const qcd_lattice* lat, int prec) {
+  return (lat && wilson_prec(prec)) ? wlinks_bytes(prec, lat->V) : 0;
+}
+
+int qcd_wilson_load_links(qcd_lattice* lat, const void* links_dev, void* packed_dev, int prec, void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(links_dev, "links_dev")) return rc;
+  if (int rc = check_dev_ptr(packed_dev, "packed_dev")) return rc;
+  if (!wilson_prec(prec)) return invalid("Wilson links: precision must be DOUBLE or SINGLE, got %d", prec);
+  int rc = launch_wilson_pack_links(lat, links_dev, packed_dev, prec, as_stream(stream));
+  if (rc) return rc;
+  lat->wilson_links[prec] = packed_dev;
+  return QCD_OK;
+}
+
+int qcd_wilson_pack_field(const qcd_lattice* lat, void* packed_dev, const void* canonical_dev, int prec, void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(packed_dev, "packed_dev")) return rc;
+  if (int rc = check_dev_ptr(canonical_dev, "canonical_dev")) return rc;
+  if (!wilson_prec(prec)) return invalid("Wilson fields: precision must be DOUBLE or SINGLE, got %d", prec);
+  return launch_wilson_pack(lat, packed_dev, canonical_dev, prec, false, as_stream(stream));
+}
+
+int qcd_wilson_unpack_field(const qcd_lattice* lat, void* canonical_dev, const void* packed_dev, int prec, void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(packed_dev, "packed_dev")) return rc;
+  if (int rc = check_dev_ptr(canonical_dev, "canonical_dev")) return rc;
+  if (!wilson_prec(prec)) return invalid("Wilson fields: precision must be DOUBLE or SINGLE, got %d", prec);
+  return launch_wilson_pack(lat, const_cast<void*>(packed_dev), canonical_dev, prec, true, as_stream(stream));
+}
+
+int qcd_wilson_op(const qcd_lattice* lat, void* out_dev, const void* in_dev, double kappa, int op, int prec,
+                  void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(out_dev, "out_dev")) return rc;
+  if (int rc = check_dev_ptr(in_dev, "in_dev")) return rc;
+  if (out_dev == in_dev) return invalid("out_dev must not alias in_dev");
+  if (op < QCD_WILSON_DSLASH || op > QCD_WILSON_MDAG) return invalid("op must be 0 (D_W), 1 (M) or 2 (M^dagger)");
+  if (!std::isfinite(kappa)) return invalid("kappa must be finite");
+  if (!wilson_prec(prec)) return invalid("Wilson operator: precision must be DOUBLE or SINGLE, got %d", prec);
+  if (!lat->wilson_links[prec]) {
+    set_error("no Wilson links loaded for precision %d (call qcd_wilson_load_links first)", prec);
+    return QCD_ERR_NO_LINKS;
+  }
+  return launch_wilson_op(lat, out_dev, in_dev, kappa, op, prec, as_stream(stream));
+}
+
+size_t qcd_wilson_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts) {
+  if (!lat) return 0;
+  qcd_solver_opts o;
+  qcd_solver_opts_default(&o);
+  if (opts) o = *opts;
+  return wilson_prec(o.prec_inner) ? wilson_workspace_bytes(lat, o.prec_inner) : 0;
+}
+
+int qcd_wilson_cgnr(qcd_lattice* lat, void* x_dev, const void* b_dev, double kappa, double tol, int max_iter,
+                    const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (info) std::memset(info, 0, sizeof(*info));
+  auto done = [&](int rc) {
+    if (info) {
+      info->status = rc;
+      info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return rc;
+  };
+  if (!lat) return done(invalid("lat is NULL"));
+  if (int rc = check_dev_ptr(x_dev, "x_dev")) return done(rc);
+  if (int rc = check_dev_ptr(b_dev, "b_dev")) return done(rc);
+  if (int rc = check_dev_ptr(workspace_dev, "workspace_dev")) return done(rc);
+  if (x_dev == b_dev) return done(invalid("x_dev must not alias b_dev"));
+  if (!std::isfinite(kappa)) return done(invalid("kappa must be finite"));
+  if (!(tol > 0.0) || !(tol < 1.0)) return done(invalid("tol must be in (0, 1), got %g", tol));
+  if (max_iter < 1) return done(invalid("max_iter must be >= 1, got %d", max_iter));
+  qcd_solver_opts o;
+  qcd_solver_opts_default(&o);
+  if (opts) o = *opts;
+  if (!wilson_prec(o.prec_inner)) return done(invalid("Wilson CGNR: inner precision must be DOUBLE or SINGLE"));
+  if (o.reliable_delta < 0.0 || o.reliable_delta >= 1.0) return done(invalid("reliable_delta must be in [0, 1)"));
+  if (!lat->wilson_links[QCD_PREC_DOUBLE] || !lat->wilson_links[o.prec_inner]) {
+    set_error("Wilson links must be loaded at FP64 and at the inner precision");
+    return done(QCD_ERR_NO_LINKS);
+  }
+  return done(run_wilson_cgnr(lat, x_dev, b_dev, kappa, tol, max_iter, o, workspace_dev, info, as_stream(stream)));
 }
 
 }  // extern "C"

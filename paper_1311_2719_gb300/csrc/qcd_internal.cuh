@@ -33,6 +33,7 @@ struct qcd_lattice {
   int tbc;
   int device;
   qcd::LinkSet links[4];  // indexed by precision
+  void* wilson_links[2] = {nullptr, nullptr};  // Wilson operator links, FP64 / FP32 (caller-owned)
 };
 
 namespace qcd {

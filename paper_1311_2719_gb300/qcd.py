@@ -104,6 +104,15 @@ SIGNATURES = {
     "qcd_workspace_bytes_full": (_sz, [_vp, ctypes.POINTER(qcd_solver_opts)]),
     "qcd_solve_full": (_i, [_vp, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp,
                             ctypes.POINTER(qcd_solve_info), _vp]),
+    "qcd_wilson_field_bytes": (_sz, [_vp, _i]),
+    "qcd_wilson_links_bytes": (_sz, [_vp, _i]),
+    "qcd_wilson_load_links": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qcd_wilson_pack_field": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qcd_wilson_unpack_field": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qcd_wilson_op": (_i, [_vp, _vp, _vp, _d, _i, _i, _vp]),
+    "qcd_wilson_workspace_bytes": (_sz, [_vp, ctypes.POINTER(qcd_solver_opts)]),
+    "qcd_wilson_cgnr": (_i, [_vp, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp,
+                             ctypes.POINTER(qcd_solve_info), _vp]),
     "qcd_tune_mrhs": (_i, [_vp, _i, _vp, _vp, _d, ctypes.POINTER(qcd_solver_opts), _vp, ctypes.c_char_p,
                            ctypes.POINTER(_i), _vp]),
     "qcd_tune_batched": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
@@ -296,6 +305,52 @@ def qcd_solve_full(lat, x_dev, b_dev, mass, tol, max_iter, opts, workspace_dev, 
                              ctypes.byref(info), _stream(stream))
     if rc in raise_on:
         _check(rc, "qcd_solve_full")
+    return rc, info.as_dict()
+
+
+QCD_WILSON_DSLASH, QCD_WILSON_M, QCD_WILSON_MDAG = 0, 1, 2
+
+
+def qcd_wilson_field_bytes(lat, prec) -> int:
+    return _lib.qcd_wilson_field_bytes(lat, prec)
+
+
+def qcd_wilson_links_bytes(lat, prec) -> int:
+    return _lib.qcd_wilson_links_bytes(lat, prec)
+
+
+def qcd_wilson_load_links(lat, links_dev, packed_dev, prec, stream=None):
+    return _check(_lib.qcd_wilson_load_links(lat, _ptr(links_dev), _ptr(packed_dev), prec, _stream(stream)),
+                  "qcd_wilson_load_links")
+
+
+def qcd_wilson_pack_field(lat, packed_dev, canonical_dev, prec, stream=None):
+    return _check(_lib.qcd_wilson_pack_field(lat, _ptr(packed_dev), _ptr(canonical_dev), prec, _stream(stream)),
+                  "qcd_wilson_pack_field")
+
+
+def qcd_wilson_unpack_field(lat, canonical_dev, packed_dev, prec, stream=None):
+    return _check(_lib.qcd_wilson_unpack_field(lat, _ptr(canonical_dev), _ptr(packed_dev), prec, _stream(stream)),
+                  "qcd_wilson_unpack_field")
+
+
+def qcd_wilson_op(lat, out_dev, in_dev, kappa, op, prec, stream=None):
+    return _check(_lib.qcd_wilson_op(lat, _ptr(out_dev), _ptr(in_dev), float(kappa), int(op), prec, _stream(stream)),
+                  "qcd_wilson_op")
+
+
+def qcd_wilson_workspace_bytes(lat, opts=None) -> int:
+    return _lib.qcd_wilson_workspace_bytes(lat, ctypes.byref(opts) if opts is not None else None)
+
+
+def qcd_wilson_cgnr(lat, x_dev, b_dev, kappa, tol, max_iter, opts, workspace_dev, stream=None,
+                    raise_on=(QCD_ERR_INVALID_ARG, QCD_ERR_CUDA, QCD_ERR_UNSUPPORTED, QCD_ERR_NO_LINKS)):
+    info = qcd_solve_info()
+    rc = _lib.qcd_wilson_cgnr(lat, _ptr(x_dev), _ptr(b_dev), float(kappa), float(tol), int(max_iter),
+                              ctypes.byref(opts) if opts is not None else None, _ptr(workspace_dev),
+                              ctypes.byref(info), _stream(stream))
+    if rc in raise_on:
+        _check(rc, "qcd_wilson_cgnr")
     return rc, info.as_dict()
 
 
