@@ -25,6 +25,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -55,8 +57,12 @@ WORKLOADS = {
                             inner="single12", nrhs=16,
                             desc="staggered 24^4 Haar, m=0.05, 16 RHS in one multi-RHS CG: FP32 recon-12 inner, "
                                  "FP64 reliable updates"),
+    "wilson32c64_8rhs": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
+                             inner="single18", nrhs=8,
+                             desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, 8 RHS in one multi-RHS CGNR on M^dagger M: "
+                                  "FP32 recursion with FP64 reliable updates, to 1e-10"),
     "wilson32c64_single": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
-                               inner="single18",
+                               inner="single18", nrhs=1,
                                desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion with "
                                     "FP64 reliable updates, to 1e-10"),
     "batch64_single12": dict(kind_solve="batched", n=64, tol=1e-10, inner="single12",
@@ -506,10 +512,18 @@ def run_gpu_batched(args, wl):
 WILSON_FLOP_PER_SITE = 1320
 
 
+def _wilson_dw_count(info):
+    """FP32/FP64 D_W applications of one RHS's CGNR: M and M^dagger per iteration, M^dagger b at
+    start-up, M and M^dagger per reliable update (the convergence check included)."""
+    return 2 * info["iterations"] + 1 + 2 * info["reliable_updates"]
+
+
 def run_gpu_wilson(args, wl):
-    """Wilson CGNR (M = 1 - kappa D_W, full lattice). One step = pack the links at FP64 and FP32 and
-    run the mixed CGNR; value = Wilson Dslash GFLOP/s inside the solve (1320 flop per site per D_W,
-    two D_W per iteration plus the FP64 reliable updates). The plain FP64 CGNR is timed beside."""
+    """Wilson CGNR (M = 1 - kappa D_W on the full lattice) on nrhs right-hand sides in one multi-RHS
+    solve. One step = pack the links at FP64 and FP32 and run the mixed CGNR on every RHS; value =
+    Wilson D_W GFLOP/s inside the solve (1320 flop per site per D_W application). The same RHS solved
+    by plain FP64 CGNR on the GPU are timed beside, with the speedup."""
+    import numpy as np
     import torch
 
     from paper_1311_2719_gb300 import inputs as I
@@ -520,42 +534,64 @@ def run_gpu_wilson(args, wl):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dims, kappa, tol = wl["dims"], wl["kappa"], wl["tol"]
+    dims, kappa, tol, R = wl["dims"], wl["kappa"], wl["tol"], wl["nrhs"]
     stream = torch.cuda.Stream()
     lat = Q.Lattice(dims)
-    U_dev = torch.from_numpy(I.make_links(dims, kind=wl["kind"], seed=1)).cuda()
-    b_dev = torch.from_numpy(I.make_spinor(dims, seed=2)).cuda()
+    V = lat.V
+    U_np = I.make_links(dims, kind=wl["kind"], seed=1)
+    U_host = torch.from_numpy(U_np).pin_memory()
+    b_host = torch.from_numpy(np.stack([I.make_spinor(dims, seed=2 + k) for k in range(R)])).pin_memory()
+    U_dev = U_host.to("cuda")
+    b_dev = b_host.to("cuda")
     x_dev = torch.zeros_like(b_dev)
+    x_host = torch.empty_like(b_host).pin_memory()
     bufs = {p: lat.empty_bytes(Q.qcd_wilson_links_bytes(lat.handle, p)) for p in (0, 1)}
+    opts = Q.qcd_solver_opts_default()
+    ws = {}
+    for p in (0, 1):
+        opts.prec_inner = p
+        ws[p] = lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    launches_links = 2
 
-    def solve(prec):
-        opts = Q.qcd_solver_opts_default()
+    def solve(prec, host_io=False, profile=False):
         opts.prec_inner = prec
-        ws = lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts))
+        opts.profile = 1 if profile else 0
         with torch.cuda.stream(stream):
+            if host_io:
+                U_dev.copy_(U_host, non_blocking=True)
+                b_dev.copy_(b_host, non_blocking=True)
             for p, buf in bufs.items():
                 Q.qcd_wilson_load_links(lat.handle, U_dev, buf, p, stream)
-            rc, info = Q.qcd_wilson_cgnr(lat.handle, x_dev, b_dev, kappa, tol, 100000, opts, ws, stream=stream)
+            rc, infos = Q.qcd_wilson_cgnr_mrhs(lat.handle, R, x_dev, b_dev, kappa, tol, 100000, opts, ws[prec],
+                                               stream=stream)
+            if host_io:
+                x_host.copy_(x_dev, non_blocking=True)
         if rc != Q.QCD_OK:
-            raise RuntimeError(f"Wilson CGNR failed: {Q.qcd_status_string(rc)} {info}")
-        return info
+            raise RuntimeError(f"Wilson CGNR failed: {Q.qcd_status_string(rc)} {infos}")
+        return infos
 
-    def timed(prec, n):
-        ms, infos = [], []
+    def timed(prec, n, host_io=False, profile=False):
+        ms, runs = [], []
         for _ in range(n):
             flush.fill_(1)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            infos.append(solve(prec))
+            runs.append(solve(prec, host_io, profile))
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        return ms, infos
+        return ms, runs
+
+    def flops_of(runs):
+        return sum(WILSON_FLOP_PER_SITE * V * _wilson_dw_count(i) for infos in runs for i in infos)
 
     for _ in range(args.warmup):
         solve(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -563,37 +599,134 @@ def run_gpu_wilson(args, wl):
         uuid = None
     proc, cpath = _clock_sampler(uuid)
     time.sleep(0.3)
-    ms, infos = timed(1, args.steps)
+    ms, runs = timed(1, args.steps)
     clocks = _clock_summary(proc, cpath)
+    if world > 1:
+        dist.barrier()
+    ms_prof, runs_prof = timed(1, max(1, min(args.steps, 3)), profile=True)
+    ms_e2e, runs_e2e = timed(1, args.steps, host_io=True)
     solve(0)
-    ms64, infos64 = timed(0, max(1, min(args.steps, 2)))
-    V = lat.V
-    flops = sum(WILSON_FLOP_PER_SITE * V * (2 * i["iterations"] + 2 * i["reliable_updates"] + 4) for i in infos)
-    tot = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
-    fl = torch.tensor([float(flops)], dtype=torch.float64, device="cuda")
+    ms64, runs64 = timed(0, max(1, min(args.steps, 2)))
+
+    # operator kernels alone (CUDA events on the launching stream, L2 flushed before each)
+    def op_time(prec, nrhs, reps=5):
+        fb = Q.qcd_wilson_field_bytes(lat.handle, prec)
+        fin, fout = lat.empty_bytes(nrhs * fb), lat.empty_bytes(nrhs * fb)
+        with torch.cuda.stream(stream):
+            for k in range(nrhs):
+                Q.qcd_wilson_pack_field(lat.handle, fin[k * fb:(k + 1) * fb], b_dev[k], prec, stream)
+        t = []
+        for _ in range(reps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if nrhs == 1:
+                Q.qcd_wilson_op(lat.handle, fout, fin, kappa, Q.QCD_WILSON_M, prec, stream)
+            else:
+                Q.qcd_wilson_op_mrhs(lat.handle, fout, fin, nrhs, kappa, Q.QCD_WILSON_M, prec, stream)
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return statistics.median(t)
+
+    t_op64 = op_time(0, 1)
+    t_op32 = op_time(1, 1)
+    t_op32_r = op_time(1, R) if R > 1 else t_op32
+
+    tot = torch.tensor([sum(ms), sum(ms_e2e)], dtype=torch.float64, device="cuda")
+    fl = torch.tensor([float(flops_of(runs)), float(flops_of(runs_e2e))], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(tot, op=dist.ReduceOp.MAX)
         dist.all_reduce(fl, op=dist.ReduceOp.SUM)
+    total_ms, total_ms_e2e = tot.tolist()
+    value = fl[0].item() / (total_ms * 1e-3) / 1e9
+    e2e_value = fl[1].item() / (total_ms_e2e * 1e-3) / 1e9
     t_mixed, t_64 = sum(ms) / len(ms), sum(ms64) / len(ms64)
+
+    # roofline of the FP32 operator launches inside the solve (K1: t = M p, K2: M^dagger t + update).
+    # Algorithmic bytes: the links once per launch (4 links x 72 B per site, FP32 recon-18) and, per
+    # running RHS and site, K1 = p (in) + t (out) = 192 B, K2 = t (in) + p + r, x (read, written) = 576 B.
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    link_b, k1_b, k2_b = 288, 192, 576
+    d_ms = sum(infos[0]["dslash_ms"] for infos in runs_prof)
+    d_launches = sum(infos[0]["dslash_launches"] for infos in runs_prof)
+    pairs = sum(max(i["iterations"] for i in infos) for infos in runs_prof)
+    rhs_its = sum(i["iterations"] for infos in runs_prof for i in infos)
+    alg = V * (2 * link_b * pairs + (k1_b + k2_b) * rhs_its)
+    achieved = alg / (d_ms * 1e-3) / 1e9
+    op_flops = WILSON_FLOP_PER_SITE * V
     out = {
-        "metric": METRIC, "value": round(fl.item() / (tot.item() * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_mixed, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (FP64 reliable updates)", "data": "synthetic (seeded Haar SU(3) links, Gaussian spinor)",
-        "config": {"workload": wl["desc"], "dims": list(dims), "kappa": kappa, "tol": tol,
+        "dtype": "f32 (FP64 reliable updates)", "data": "synthetic (seeded Haar SU(3) links, Gaussian spinors)",
+        "config": {"workload": wl["desc"], "dims": list(dims), "kappa": kappa, "tol": tol, "nrhs": R,
                    "parallelism": f"replicas x{world} (no sharding)",
                    "l2": "flushed before every step (512 MB write, outside the timed events)",
-                   "step": "qcd_wilson_load_links (FP64 + FP32) + qcd_wilson_cgnr"},
-        "cg": {"iterations": infos[-1]["iterations"], "true_rel_residual": infos[-1]["true_rel_residual"],
-               "reliable_updates": infos[-1]["reliable_updates"], "time_to_solution_ms": round(t_mixed, 4),
-               "plain_fp64_cgnr_ms": round(t_64, 4), "plain_fp64_iterations": infos64[-1]["iterations"],
+                   "step": "qcd_wilson_load_links (FP64 + FP32) + qcd_wilson_cgnr_mrhs"},
+        "cg": {"iterations": [i["iterations"] for i in runs[-1]],
+               "reliable_updates": [i["reliable_updates"] for i in runs[-1]],
+               "max_true_rel_residual": max(i["true_rel_residual"] for i in runs[-1]),
+               "time_to_solution_ms": round(t_mixed, 4), "plain_fp64_cgnr_ms": round(t_64, 4),
+               "plain_fp64_iterations": [i["iterations"] for i in runs64[-1]],
                "speedup_vs_plain_fp64_cgnr": round(t_64 / t_mixed, 3)},
-        "gpu_launches": int(sum(i["kernel_launches"] + 2 for i in infos)),
+        "roofline": {"bound": "hbm", "kernel": "wilson_mrhs_kernel (CGNR K1+K2 launches, FP32)",
+                     "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(achieved / hbm_peak, 4), "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
+                     "traffic": None, "alg_bytes_per_launch": round(alg / d_launches),
+                     "alg_bytes_per_site": {"links_per_launch": link_b, "k1_per_rhs": k1_b, "k2_per_rhs": k2_b},
+                     "avg_launch_us": round(d_ms / d_launches * 1e3, 3)},
+        "operator_alone": {
+            "fp32_M_1rhs": {"us": round(t_op32 * 1e3, 2), "gbs": round(480 * V / (t_op32 * 1e-3) / 1e9, 1),
+                            "frac_hbm": round(480 * V / (t_op32 * 1e-3) / 1e9 / hbm_peak, 4),
+                            "alg_bytes_per_site": 480},
+            f"fp32_M_{R}rhs": {"us": round(t_op32_r * 1e3, 2),
+                               "gbs": round((288 + 192 * R) * V / (t_op32_r * 1e-3) / 1e9, 1),
+                               "frac_hbm": round((288 + 192 * R) * V / (t_op32_r * 1e-3) / 1e9 / hbm_peak, 4),
+                               "alg_bytes_per_site": 288 + 192 * R},
+            "fp64_M_1rhs": {"us": round(t_op64 * 1e3, 2), "tflops": round(op_flops / (t_op64 * 1e-3) / 1e12, 4),
+                            "frac_fp64_peak": round(op_flops / (t_op64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                            "note": "FP64 D_W is FP64-pipe bound on GB300 (1320 flop vs 960 B per site)"}},
+        "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": int(U_host.numel() * 16 + b_host.numel() * 16),
+                "d2h_bytes_per_step": int(x_host.numel() * 16), "ms_per_step": round(total_ms_e2e / args.steps, 4)},
+        "gpu_launches": int(sum(launches_links + infos[0]["kernel_launches"] for infos in runs)),
         "clocks": clocks,
+        "ms_per_step_profiled": round(sum(ms_prof) / len(ms_prof), 4),
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = wilson_cpu_baseline(wl, U_np, b_host[0].numpy())
     if world > 1:
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def _wilson_oracle_sample(wl, U=None, b=None):
+    """One application of M = 1 - kappa D_W by the FP64 oracle on the full lattice (flops, seconds)."""
+    from oracle import wilson as Wo
+    from paper_1311_2719_gb300 import inputs as I
+
+    dims = wl["dims"]
+    if U is None:
+        U = I.make_links(dims, kind=wl["kind"], seed=1)
+        b = I.make_spinor(dims, seed=2)
+    t0 = time.perf_counter()
+    Wo.apply_m(U, b, dims, wl["kappa"])
+    dt = time.perf_counter() - t0
+    return WILSON_FLOP_PER_SITE * U.shape[0], dt
+
+
+def wilson_cpu_baseline(wl, U=None, b=None):
+    f, dt = _wilson_oracle_sample(wl, U, b)
+    return {"value": round(f / dt / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle: one M = 1 - kappa D_W application on the full {wl['dims']} lattice "
+                      f"({dt:.1f} s), 1320 flop/site"}
 
 
 def _oracle_sample(wl, iters, U=None, b=None):
@@ -621,32 +754,61 @@ def cpu_baseline(wl, iters):
 
 
 def run_reference(args, wl):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload per step (rank 0 only)."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return None
     from paper_1311_2719_gb300 import inputs as I
 
-    dims = wl["dims"]
-    U = I.make_links(dims, kind=wl["kind"], seed=1)
-    b = I.make_source(dims, seed=2)
+    kind = wl.get("kind_solve")
+    if kind == "wilson":
+        from oracle import wilson as Wo
+        dims = wl["dims"]
+        U = I.make_links(dims, kind=wl["kind"], seed=1)
+        b = I.make_spinor(dims, seed=2)
+        sites = np.arange(0, U.shape[0], 32)
+
+        def sample():
+            t0 = time.perf_counter()
+            Wo.dslash_w_sites(U, b, dims, sites)
+            return WILSON_FLOP_PER_SITE * len(sites), time.perf_counter() - t0
+
+        what = (f"each step: FP64 numpy oracle Wilson D_W at every 32nd site ({len(sites)} sites) of the {dims} "
+                f"lattice, 1320 flop/site, 1 thread")
+        cfg = {"dims": list(dims), "kappa": wl["kappa"], "nrhs": wl["nrhs"]}
+    else:
+        if kind == "batched":  # the largest lattice of the batch stands in for the batch
+            spec = max(I.make_lattice_batch(wl["n"], seed=4), key=lambda t: int(np.prod(t[0])))
+            owl = dict(dims=spec[0], kind="haar", mass=spec[1], tol=wl["tol"])
+            U = I.make_links(spec[0], kind="haar", seed=spec[2])
+            b = I.make_source(spec[0], seed=spec[3])
+        else:
+            owl = wl
+            U = I.make_links(wl["dims"], kind=wl["kind"], seed=1)
+            b = I.make_source(wl["dims"], seed=2)
+        n_it = [0]
+
+        def sample():
+            f, t, n_it[0] = _oracle_sample(owl, args.ref_iters, U, b)
+            return f, t
+
+        what = (f"each step: FP64 numpy oracle CG on the {tuple(owl['dims'])} lattice for {args.ref_iters} iterations "
+                f"+ y + true residual (bounded sample), 1 thread")
+        cfg = {"dims": list(owl["dims"]), "mass": owl["mass"]}
     for _ in range(args.warmup):
-        _oracle_sample(wl, 1, U, b)
+        sample()
     tot_f, tot_t = 0.0, 0.0
-    n = 0
     for _ in range(args.steps):
-        f, t, n = _oracle_sample(wl, args.ref_iters, U, b)
+        f, t = sample()
         tot_f += f
         tot_t += t
     v = tot_f / tot_t / 1e9
-    sample = (f"each step: FP64 numpy oracle CG on the {dims} workload for {n} iterations + y + true residual "
-              f"(bounded sample), 1 thread")
     return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Haar SU(3) links, Gaussian source)",
-            "config": {"workload": wl["desc"], "dims": list(dims), "mass": wl["mass"], "tol": wl["tol"],
-                       "parallelism": "cpu oracle, rank 0 only"},
-            "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": dict({"workload": wl["desc"], "tol": wl["tol"], "parallelism": "cpu oracle, rank 0 only"}, **cfg),
+            "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": what},
             "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

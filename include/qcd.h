@@ -270,12 +270,38 @@ QCD_API int qcd_wilson_unpack_field(const qcd_lattice* lat, void* canonical_dev,
  * A spin-projected kernel: each hop multiplies two colour vectors by the link. */
 QCD_API int qcd_wilson_op(const qcd_lattice* lat, void* out_dev, const void* in_dev, double kappa, int op, int prec,
                   void* stream);
-QCD_API size_t qcd_wilson_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts);
+/* The same operator on nrhs right-hand sides at once: nrhs packed fields back to back
+ * (nrhs * qcd_wilson_field_bytes bytes each side); every link is loaded once per register block of
+ * right-hand sides (2 in SINGLE, 1 in DOUBLE) and applied to all of them. 1 <= nrhs <= 16. */
+QCD_API int qcd_wilson_op_mrhs(const qcd_lattice* lat, void* out_dev, const void* in_dev, int nrhs, double kappa,
+                       int op, int prec, void* stream);
+/* Bytes of the device workspace qcd_wilson_cgnr (nrhs = 1) or qcd_wilson_cgnr_mrhs needs for these
+ * options; 0 on a bad argument (nrhs outside [1, 16], unsupported precision). */
+QCD_API size_t qcd_wilson_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts, int nrhs);
 /* CGNR: M^dagger M x = M^dagger b to |M^dagger b - M^dagger M x| / |M^dagger b| <= tol (recomputed in FP64,
- * returned in info->true_rel_residual); canonical spinor fields. opts->prec_inner = SINGLE runs the
- * recursion in FP32 with FP64 reliable updates (links loaded at both precisions). */
+ * returned in info->true_rel_residual); canonical spinor fields complex128[V][4][3].
+ * opts->prec_inner = SINGLE runs the recursion in FP32 with reliable updates (opts->reliable_delta,
+ * opts->reliable_interval; links loaded at both precisions): each update folds the FP32 increment
+ * into the FP64 solution, recomputes the true residual b - M x in FP64 and restarts the recursion
+ * from M^dagger (b - M x); a RHS stops only after the full FP64 residual of the normal equations
+ * confirms the tolerance. DOUBLE runs plain FP64 CGNR, confirmed the same way. Synchronises `stream`.
+ * Returns QCD_ERR_NOT_CONVERGED when max_iter runs out, QCD_ERR_BREAKDOWN on a non-finite or
+ * non-positive CG scalar. */
 QCD_API int qcd_wilson_cgnr(qcd_lattice* lat, void* x_dev, const void* b_dev, double kappa, double tol, int max_iter,
                     const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream);
+/* nrhs independent CGNR solves on one lattice in one set of launches: each loaded link is applied to
+ * a register block of right-hand sides (opts->rhs_block: 0 = 2 in SINGLE / 1 in DOUBLE; 1, 2, 4 in
+ * SINGLE; 1, 2 in DOUBLE), each RHS keeps its own scalars, reliable updates and exit.
+ *   x_dev, b_dev  : nrhs canonical fields back to back, complex128[nrhs][V][4][3].
+ *   workspace_dev : qcd_wilson_workspace_bytes(lat, opts, nrhs) bytes.
+ *   info          : optional array of nrhs entries; the launch counters and, with opts->profile, the
+ *                   summed time of the operator launches (dslash_ms over dslash_launches) are
+ *                   reported on entry 0.
+ * 1 <= nrhs <= 16. Returns QCD_OK when every RHS converged, else the first failing status
+ * (QCD_ERR_BREAKDOWN takes precedence). Synchronises `stream`. */
+QCD_API int qcd_wilson_cgnr_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, double kappa, double tol,
+                         int max_iter, const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info,
+                         void* stream);
 
 /* ---- autotuning of launch shapes (no counterpart in the paper) ------------------------------ */
 

@@ -37,11 +37,13 @@ int run_cg(qcd_lattice*, void*, const void*, double, double, int, const qcd_solv
 size_t batch_workspace_bytes(int, const qcd_lattice* const*, int);
 size_t wfield_bytes(int, long long);
 size_t wlinks_bytes(int, long long);
-size_t wilson_workspace_bytes(const qcd_lattice*, int);
+size_t wilson_workspace_bytes(const qcd_lattice*, int, int);
+int wilson_rhs_block(int, int, int);
+int launch_wilson_op_mrhs(const qcd_lattice*, void*, const void*, int, double, int, int, cudaStream_t);
 int launch_wilson_pack_links(const qcd_lattice*, const void*, void*, int, cudaStream_t);
 int launch_wilson_pack(const qcd_lattice*, void*, const void*, int, bool, cudaStream_t);
 int launch_wilson_op(const qcd_lattice*, void*, const void*, double, int, int, cudaStream_t);
-int run_wilson_cgnr(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*,
+int run_wilson_cgnr(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*,
                     qcd_solve_info*, cudaStream_t);
 size_t full_workspace_bytes(const qcd_lattice*, int);
 int run_solve_full(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*,
@@ -443,8 +445,7 @@ int qcd_wilson_unpack_field(const qcd_lattice* lat, void* canonical_dev, const v
   return launch_wilson_pack(lat, const_cast<void*>(packed_dev), canonical_dev, prec, true, as_stream(stream));
 }
 
-int qcd_wilson_op(const qcd_lattice* lat, void* out_dev, const void* in_dev, double kappa, int op, int prec,
-                  void* stream) {
+static int check_wilson_op(const qcd_lattice* lat, void* out_dev, const void* in_dev, double kappa, int op, int prec) {
   if (!lat) return invalid("lat is NULL");
   if (int rc = check_dev_ptr(out_dev, "out_dev")) return rc;
   if (int rc = check_dev_ptr(in_dev, "in_dev")) return rc;
@@ -456,29 +457,48 @@ int qcd_wilson_op(const qcd_lattice* lat, void* out_dev, const void* in_dev, dou
     set_error("no Wilson links loaded for precision %d (call qcd_wilson_load_links first)", prec);
     return QCD_ERR_NO_LINKS;
   }
+  return QCD_OK;
+}
+
+int qcd_wilson_op(const qcd_lattice* lat, void* out_dev, const void* in_dev, double kappa, int op, int prec,
+                  void* stream) {
+  if (int rc = check_wilson_op(lat, out_dev, in_dev, kappa, op, prec)) return rc;
   return launch_wilson_op(lat, out_dev, in_dev, kappa, op, prec, as_stream(stream));
 }
 
-size_t qcd_wilson_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts) {
-  if (!lat) return 0;
+int qcd_wilson_op_mrhs(const qcd_lattice* lat, void* out_dev, const void* in_dev, int nrhs, double kappa, int op,
+                       int prec, void* stream) {
+  if (int rc = check_wilson_op(lat, out_dev, in_dev, kappa, op, prec)) return rc;
+  if (nrhs < 1 || nrhs > kMaxRhs) return invalid("nrhs must be in [1, %d], got %d", kMaxRhs, nrhs);
+  return launch_wilson_op_mrhs(lat, out_dev, in_dev, nrhs, kappa, op, prec, as_stream(stream));
+}
+
+size_t qcd_wilson_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts, int nrhs) {
+  if (!lat || nrhs < 1 || nrhs > kMaxRhs) return 0;
   qcd_solver_opts o;
   qcd_solver_opts_default(&o);
   if (opts) o = *opts;
-  return wilson_prec(o.prec_inner) ? wilson_workspace_bytes(lat, o.prec_inner) : 0;
+  return wilson_prec(o.prec_inner) ? wilson_workspace_bytes(lat, o.prec_inner, nrhs) : 0;
 }
 
-int qcd_wilson_cgnr(qcd_lattice* lat, void* x_dev, const void* b_dev, double kappa, double tol, int max_iter,
-                    const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream) {
+static int wilson_cgnr_common(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, double kappa, double tol,
+                              int max_iter, const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info,
+                              void* stream) {
   const auto t0 = std::chrono::steady_clock::now();
-  if (info) std::memset(info, 0, sizeof(*info));
+  const int n_info = (nrhs >= 1 && nrhs <= kMaxRhs) ? nrhs : 1;
+  if (info) std::memset(info, 0, sizeof(*info) * n_info);
   auto done = [&](int rc) {
     if (info) {
-      info->status = rc;
-      info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      for (int q = 0; q < n_info; ++q) {
+        if (rc != QCD_OK && info[q].status == QCD_OK && !info[q].converged) info[q].status = rc;
+        info[q].seconds = sec;
+      }
     }
     return rc;
   };
   if (!lat) return done(invalid("lat is NULL"));
+  if (nrhs < 1 || nrhs > kMaxRhs) return done(invalid("nrhs must be in [1, %d], got %d", kMaxRhs, nrhs));
   if (int rc = check_dev_ptr(x_dev, "x_dev")) return done(rc);
   if (int rc = check_dev_ptr(b_dev, "b_dev")) return done(rc);
   if (int rc = check_dev_ptr(workspace_dev, "workspace_dev")) return done(rc);
@@ -491,11 +511,26 @@ int qcd_wilson_cgnr(qcd_lattice* lat, void* x_dev, const void* b_dev, double kap
   if (opts) o = *opts;
   if (!wilson_prec(o.prec_inner)) return done(invalid("Wilson CGNR: inner precision must be DOUBLE or SINGLE"));
   if (o.reliable_delta < 0.0 || o.reliable_delta >= 1.0) return done(invalid("reliable_delta must be in [0, 1)"));
+  if (wilson_rhs_block(o.prec_inner, nrhs, o.rhs_block) < 1)
+    return done(invalid("rhs_block %d is not supported for Wilson precision %d (1, 2 or 4 for SINGLE; 1 or 2 for DOUBLE)",
+                        o.rhs_block, o.prec_inner));
   if (!lat->wilson_links[QCD_PREC_DOUBLE] || !lat->wilson_links[o.prec_inner]) {
     set_error("Wilson links must be loaded at FP64 and at the inner precision");
     return done(QCD_ERR_NO_LINKS);
   }
-  return done(run_wilson_cgnr(lat, x_dev, b_dev, kappa, tol, max_iter, o, workspace_dev, info, as_stream(stream)));
+  return done(run_wilson_cgnr(lat, nrhs, x_dev, b_dev, kappa, tol, max_iter, o, workspace_dev, info,
+                              as_stream(stream)));
+}
+
+int qcd_wilson_cgnr(qcd_lattice* lat, void* x_dev, const void* b_dev, double kappa, double tol, int max_iter,
+                    const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream) {
+  return wilson_cgnr_common(lat, 1, x_dev, b_dev, kappa, tol, max_iter, opts, workspace_dev, info, stream);
+}
+
+int qcd_wilson_cgnr_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, double kappa, double tol,
+                         int max_iter, const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info,
+                         void* stream) {
+  return wilson_cgnr_common(lat, nrhs, x_dev, b_dev, kappa, tol, max_iter, opts, workspace_dev, info, stream);
 }
 
 }  // extern "C"

@@ -23,36 +23,6 @@ bool tune_lookup(const std::string& key, std::vector<int>* out);
 // Counter slots in sc[0] used by the multi-RHS kernels (single-RHS kernels use 0..5 of each sc[r]).
 enum { kCtrK3M = 8, kCtrK1M = 9, kCtrK2M = 10 };
 
-// Write this block's RB partial sums for RHS r0..r0+RB-1; true in the block that finishes last
-// over the whole (x, y) grid.
-template <int RB>
-__device__ __forceinline__ bool mrhs_arrive(double (&v)[RB], int r0, int nrhs, double* partials, unsigned* counter) {
-  __shared__ bool am_last;
-  block_sum<RB>(v);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < RB; ++j)
-      if (r0 + j < nrhs) partials[(size_t)(r0 + j) * kMaxPartials + blockIdx.x] = v[j];
-    __threadfence();
-    const unsigned t = atomicAdd(counter, 1u);
-    am_last = (t == gridDim.x * gridDim.y - 1);
-  }
-  __syncthreads();
-  return am_last;
-}
-
-// In the last block: tot[r] = sum over blocks of partials[r][.] in block order (deterministic).
-__device__ __forceinline__ void mrhs_totals(int nrhs, const double* partials, double* tot_smem) {
-  __threadfence();
-  for (int r = 0; r < nrhs; ++r) {
-    double s[1] = {0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[0] += __ldcg(partials + (size_t)r * kMaxPartials + b);
-    block_sum<1>(s);
-    if (threadIdx.x == 0) tot_smem[r] = s[0];
-  }
-  __syncthreads();
-}
-
 // Last node of the device-side multi-RHS loop: loop again while any right-hand side still runs.
 static __global__ void mrhs_loop_control_kernel(CgScalars* sc, int nrhs, cudaGraphConditionalHandle handle,
                                                 int max_loops) {

@@ -80,6 +80,7 @@ struct WField<QCD_PREC_DOUBLE> {
     for (int q = 0; q < 12; ++q) p[(size_t)q * V + i] = make_double2(v.s[q / 3].c[q % 3].re, v.s[q / 3].c[q % 3].im);
   }
   static size_t bytes(long long V) { return (size_t)V * 12 * sizeof(double2); }
+  __host__ __device__ WField at(int r) const { return {p + (size_t)r * 12 * V, V}; }  // RHS r of a multi-RHS field
 };
 
 template <>
@@ -105,6 +106,7 @@ struct WField<QCD_PREC_SINGLE> {
     }
   }
   static size_t bytes(long long V) { return (size_t)V * 6 * sizeof(float4); }
+  __host__ __device__ WField at(int r) const { return {p + (size_t)r * 6 * V, V}; }
 };
 
 // links [mu][9][V], zeta folded into the t-links of the last time slice (no staggered phases)
@@ -164,61 +166,75 @@ __device__ __forceinline__ void full_site(const Geom& g, int i, int c[4]) {
 }
 
 // ---------------------------------------------------------------- the hopping term at site i
-// G5IN: the input field is read as gamma5 psi (spins 2, 3 negated) — used for M^dagger.
+// neighbour of site i (coordinates c) in direction mu: dir 0 forward, dir 1 backward (periodic wrap)
+__device__ __forceinline__ int w_neighbour(const Geom& g, int i, const int c[4], int mu, int dir) {
+  const int L[4] = {g.L0, g.L1, g.L2, g.L3};
+  const int st[4] = {1, g.L0, g.L0 * g.L1, g.L0 * g.L1 * g.L2};
+  return dir == 0 ? (c[mu] == L[mu] - 1 ? i - (L[mu] - 1) * st[mu] : i + st[mu])
+                  : (c[mu] == 0 ? i + (L[mu] - 1) * st[mu] : i - st[mu]);
+}
+
+// One hop into acc: forward (dir 0) adds (1 - gamma_mu) U psi, backward (dir 1) adds
+// (1 + gamma_mu) U^dagger psi, through the two-row spin projection. G5IN: psi is read as gamma5 psi
+// (spins 2, 3 negated) — used for M^dagger.
+template <bool G5IN, typename T>
+__device__ __forceinline__ void hop_accumulate(spinor<T>& acc, const su3<T>& Ul, spinor<T> psi, int mu, int dir) {
+  const int sgn = dir == 0 ? 2 : 0;  // phase code of s: -1 -> 2, +1 -> 0
+  if constexpr (G5IN) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      psi.s[2].c[a] = {-psi.s[2].c[a].re, -psi.s[2].c[a].im};
+      psi.s[3].c[a] = {-psi.s[3].c[a].re, -psi.s[3].c[a].im};
+    }
+  }
+  cvec3<T> h[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cplx<T> t = times_phase(psi.s[gcol(mu, r)].c[a], sgn + gph(mu, r));
+      h[r].c[a] = {psi.s[r].c[a].re + t.re, psi.s[r].c[a].im + t.im};
+    }
+  cvec3<T> w[2];
+  w[0] = dir == 0 ? mul(Ul, h[0]) : adj_mul(Ul, h[0]);
+  w[1] = dir == 0 ? mul(Ul, h[1]) : adj_mul(Ul, h[1]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc.s[0].c[a].re += w[0].c[a].re; acc.s[0].c[a].im += w[0].c[a].im;
+    acc.s[1].c[a].re += w[1].c[a].re; acc.s[1].c[a].im += w[1].c[a].im;
+#pragma unroll
+    for (int r = 2; r < 4; ++r) {
+      const cplx<T> t = times_phase(w[gcol(mu, r)].c[a], sgn + gph(mu, r));
+      acc.s[r].c[a].re += t.re;
+      acc.s[r].c[a].im += t.im;
+    }
+  }
+}
+
 template <class LinksT, class FieldT, bool G5IN>
 __device__ __forceinline__ spinor<typename LinksT::T> wilson_hop(const Geom& g, const LinksT& U, const FieldT& in, int i) {
   using T = typename LinksT::T;
   int c[4];
   full_site(g, i, c);
-  const int L[4] = {g.L0, g.L1, g.L2, g.L3};
-  const int st[4] = {1, g.L0, g.L0 * g.L1, g.L0 * g.L1 * g.L2};
   spinor<T> acc;
   zero(acc);
 #pragma unroll
-  for (int mu = 0; mu < 4; ++mu) {
+  for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
-    for (int dir = 0; dir < 2; ++dir) {  // dir 0: forward, (1 - gamma); dir 1: backward, (1 + gamma)
-      const int sgn = dir == 0 ? 2 : 0;   // phase code of s: -1 -> 2, +1 -> 0
-      const int nb = dir == 0 ? (c[mu] == L[mu] - 1 ? i - (L[mu] - 1) * st[mu] : i + st[mu])
-                              : (c[mu] == 0 ? i + (L[mu] - 1) * st[mu] : i - st[mu]);
-      spinor<T> psi = in.load(nb);
-      if constexpr (G5IN) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          psi.s[2].c[a] = {-psi.s[2].c[a].re, -psi.s[2].c[a].im};
-          psi.s[3].c[a] = {-psi.s[3].c[a].re, -psi.s[3].c[a].im};
-        }
-      }
-      cvec3<T> h[2];
-#pragma unroll
-      for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const cplx<T> t = times_phase(psi.s[gcol(mu, r)].c[a], sgn + gph(mu, r));
-          h[r].c[a] = {psi.s[r].c[a].re + t.re, psi.s[r].c[a].im + t.im};
-        }
-      const su3<T> Ul = U.load(mu, dir == 0 ? i : nb);
-      cvec3<T> w[2];
-      w[0] = dir == 0 ? mul(Ul, h[0]) : adj_mul(Ul, h[0]);
-      w[1] = dir == 0 ? mul(Ul, h[1]) : adj_mul(Ul, h[1]);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        acc.s[0].c[a].re += w[0].c[a].re; acc.s[0].c[a].im += w[0].c[a].im;
-        acc.s[1].c[a].re += w[1].c[a].re; acc.s[1].c[a].im += w[1].c[a].im;
-#pragma unroll
-        for (int r = 2; r < 4; ++r) {
-          const cplx<T> t = times_phase(w[gcol(mu, r)].c[a], sgn + gph(mu, r));
-          acc.s[r].c[a].re += t.re;
-          acc.s[r].c[a].im += t.im;
-        }
-      }
+    for (int dir = 0; dir < 2; ++dir) {
+      const int nb = w_neighbour(g, i, c, mu, dir);
+      hop_accumulate<G5IN>(acc, U.load(mu, dir == 0 ? i : nb), in.load(nb), mu, dir);
     }
-  }
   return acc;
 }
 
+// resident 128-thread blocks per SM: FP64 4 (at most 128 registers: 16 warps to hide the FP64
+// pipe's latency); FP32 none (0: the compiler's own choice, 80 registers without spills)
+template <typename T>
+struct WMinBlocks { static constexpr int value = sizeof(T) == 8 ? 4 : 0; };
+
 template <class LinksT, class FieldT, bool G5IN, class Epi>
-__global__ void __launch_bounds__(kBlock) wilson_kernel(Geom g, int V, LinksT U, FieldT in, Epi epi) {
+__global__ void __launch_bounds__(kBlock, WMinBlocks<typename LinksT::T>::value) wilson_kernel(Geom g, int V, LinksT U, FieldT in, Epi epi) {
   if (epi.skip()) return;
   using A = typename Accum<typename LinksT::T>::type;
   A red[Epi::NV > 0 ? Epi::NV : 1];
@@ -276,79 +292,150 @@ struct WApplyM {  // out = M in or M^dagger in
   __device__ __forceinline__ void finish(A*) const {}
 };
 
-// CGNR K1: t = M p, |t|^2 -> alpha = rr / |t|^2
+// ---------------------------------------------------------------- multi-RHS operator kernel
+// grid.y enumerates blocks of RB right-hand sides: each link is loaded once and applied to the RB
+// spinors of that block (fields of all RHS back to back, WField::at). The epilogue sees one
+// (site, RHS) pair at a time; reducing epilogues finish with one deterministic sum per RHS.
+template <class LinksT, class FieldT, bool G5IN, int RB, class Epi>
+__global__ void __launch_bounds__(kBlock) wilson_mrhs_kernel(Geom g, int V, LinksT U, FieldT in, int nrhs, Epi epi) {
+  using T = typename LinksT::T;
+  const int r0 = blockIdx.y * RB;
+  unsigned active = 0;
+#pragma unroll
+  for (int j = 0; j < RB; ++j)
+    if (r0 + j < nrhs && epi.running(r0 + j)) active |= 1u << j;
+  using A = typename Accum<T>::type;
+  A part[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) part[j] = A(0);
+  if (active) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+      int c[4];
+      full_site(g, i, c);
+      spinor<T> acc[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) zero(acc[j]);
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+          const int nb = w_neighbour(g, i, c, mu, dir);
+          const su3<T> Ul = U.load(mu, dir == 0 ? i : nb);
+#pragma unroll
+          for (int j = 0; j < RB; ++j)
+            if ((active >> j) & 1u) hop_accumulate<G5IN>(acc[j], Ul, in.at(r0 + j).load(nb), mu, dir);
+        }
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        if ((active >> j) & 1u) epi.site(i, r0 + j, acc[j], part[j]);
+    }
+  }
+  if constexpr (Epi::kReduce) {
+    double red[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) red[j] = (double)part[j];
+    if (mrhs_arrive<RB>(red, r0, nrhs, epi.partials, epi.counter())) {
+      __shared__ double tot[kMaxRhs];
+      mrhs_totals(nrhs, epi.partials, tot);
+      if (threadIdx.x == 0) {
+        for (int q = 0; q < nrhs; ++q)
+          if (epi.running(q)) epi.update(q, tot[q]);
+        *epi.counter() = 0u;
+      }
+    }
+  }
+}
+
+// counter slots of sc[0] used by the multi-RHS CGNR kernels (the FP64 residual epilogue uses slot 4 of sc[r])
+enum { kCtrWT = 9, kCtrWU = 10 };
+
+// out_r = D_W in_r (op 0), M in_r (op 1), M^dagger in_r (op 2, with G5IN)
+template <class FieldT, int OP>
+struct WOpM {
+  static constexpr bool kReduce = false;
+  FieldT in, out;
+  double kappa;
+  double* partials;
+  __device__ __forceinline__ bool running(int) const { return true; }
+  __device__ __forceinline__ unsigned* counter() const { return nullptr; }
+  template <class T, class A>
+  __device__ __forceinline__ void site(int i, int r, const spinor<T>& acc, A&) const {
+    if constexpr (OP == 0) out.at(r).store(i, acc);
+    else out.at(r).store(i, m_combine<FieldT, OP == 2>(in.at(r), i, acc, (T)kappa));
+  }
+  __device__ __forceinline__ void update(int, double) const {}
+};
+
+// CGNR K1: t_r = M p_r, |t_r|^2 -> alpha_r = rr_r / |t_r|^2
 template <class FieldT>
 struct WEpiT {
-  static constexpr int NV = 1;
+  static constexpr bool kReduce = true;
   FieldT p, t;
   double kappa;
   CgScalars* sc;
   double* partials;
-  __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
+  __device__ __forceinline__ bool running(int r) const { return sc[r].done == kRunning; }
+  __device__ __forceinline__ unsigned* counter() const { return &sc[0].counter[kCtrWT]; }
   template <class T, class A>
-  __device__ __forceinline__ void site(int i, spinor<T>& acc, A* red) const {
-    const spinor<T> v = m_combine<FieldT, false>(p, i, acc, (T)kappa);
-    t.store(i, v);
-    accum(red[0], norm2(v));
+  __device__ __forceinline__ void site(int i, int r, const spinor<T>& acc, A& red) const {
+    const spinor<T> v = m_combine<FieldT, false>(p.at(r), i, acc, (T)kappa);
+    t.at(r).store(i, v);
+    accum(red, norm2(v));
   }
-  template <class A>
-  __device__ __forceinline__ void finish(A* red) const {
-    double v[1] = {(double)red[0]}, tot[1];
-    if (grid_sum_last_block<1>(v, partials, &sc->counter[2], tot) && threadIdx.x == 0) {
-      const double alpha = sc->rr / tot[0];
-      if (!(tot[0] > 0.0) || !isfinite(alpha)) sc->done = kBreakdown;
-      else sc->alpha = alpha;
-    }
+  __device__ __forceinline__ void update(int r, double tt) const {
+    CgScalars& s = sc[r];
+    const double alpha = s.rr / tt;
+    if (!(tt > 0.0) || !isfinite(alpha)) s.done = kBreakdown;
+    else s.alpha = alpha;
   }
 };
 
-// CGNR K2: s = M^dagger t; x += alpha p; r -= alpha s; |r|^2 -> beta and the exit tests
+// CGNR K2: s = M^dagger t_r; x_r += alpha_r p_r; r_r -= alpha_r s; |r_r|^2 -> beta_r and the exit tests
 template <class FieldT, class XFieldT>
 struct WEpiUpdate {
-  static constexpr int NV = 1;
+  static constexpr bool kReduce = true;
   FieldT t, p, r;
   XFieldT x;
   double kappa;
   CgScalars* sc;
   double* partials;
-  __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
+  __device__ __forceinline__ bool running(int q) const { return sc[q].done == kRunning; }
+  __device__ __forceinline__ unsigned* counter() const { return &sc[0].counter[kCtrWU]; }
   template <class T, class A>
-  __device__ __forceinline__ void site(int i, spinor<T>& acc, A* red) const {
+  __device__ __forceinline__ void site(int i, int q, const spinor<T>& acc, A& red) const {
     using TX = typename XFieldT::T;
-    const spinor<T> s = m_combine<FieldT, true>(t, i, acc, (T)kappa);
-    const T alpha = (T)sc->alpha;
-    const spinor<T> pv = p.load(i);
-    spinor<T> rv = r.load(i);
-    spinor<TX> xv = x.load(i);
+    const spinor<T> s = m_combine<FieldT, true>(t.at(q), i, acc, (T)kappa);
+    const T alpha = (T)sc[q].alpha;
+    const FieldT rf = r.at(q);
+    const XFieldT xf = x.at(q);
+    const spinor<T> pv = p.at(q).load(i);
+    spinor<T> rv = rf.load(i);
+    spinor<TX> xv = xf.load(i);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        rv.s[q].c[a].re = fma(-alpha, s.s[q].c[a].re, rv.s[q].c[a].re);
-        rv.s[q].c[a].im = fma(-alpha, s.s[q].c[a].im, rv.s[q].c[a].im);
-        xv.s[q].c[a].re = fma((TX)alpha, (TX)pv.s[q].c[a].re, xv.s[q].c[a].re);
-        xv.s[q].c[a].im = fma((TX)alpha, (TX)pv.s[q].c[a].im, xv.s[q].c[a].im);
+        rv.s[u].c[a].re = fma(-alpha, s.s[u].c[a].re, rv.s[u].c[a].re);
+        rv.s[u].c[a].im = fma(-alpha, s.s[u].c[a].im, rv.s[u].c[a].im);
+        xv.s[u].c[a].re = fma((TX)alpha, (TX)pv.s[u].c[a].re, xv.s[u].c[a].re);
+        xv.s[u].c[a].im = fma((TX)alpha, (TX)pv.s[u].c[a].im, xv.s[u].c[a].im);
       }
-    r.store(i, rv);
-    x.store(i, xv);
-    accum(red[0], norm2(rv));
+    rf.store(i, rv);
+    xf.store(i, xv);
+    accum(red, norm2(rv));
   }
-  template <class A>
-  __device__ __forceinline__ void finish(A* red) const {
-    double v[1] = {(double)red[0]}, tot[1];
-    if (grid_sum_last_block<1>(v, partials, &sc->counter[3], tot) && threadIdx.x == 0) {
-      const double rr = tot[0];
-      sc->iter += 1;
-      sc->since_ru += 1;
-      sc->rr_prev = sc->rr;
-      sc->rr = rr;
-      if (!isfinite(rr)) { sc->done = kBreakdown; return; }
-      sc->beta = rr / sc->rr_prev;
-      if (rr > sc->rmax2) sc->rmax2 = rr;
-      if (rr < sc->delit) sc->done = kConverged;
-      else if (sc->iter >= sc->max_iter) sc->done = kMaxIter;
-      else if (sc->mixed && (sc->since_ru >= sc->ru_interval || rr < sc->delta2 * sc->rmax2)) sc->done = kReliable;
-    }
+  __device__ __forceinline__ void update(int q, double rr) const {
+    CgScalars& s = sc[q];
+    s.iter += 1;
+    s.since_ru += 1;
+    s.rr_prev = s.rr;
+    s.rr = rr;
+    if (!isfinite(rr)) { s.done = kBreakdown; return; }
+    s.beta = rr / s.rr_prev;
+    if (rr > s.rmax2) s.rmax2 = rr;
+    if (rr < s.delit) s.done = kConverged;
+    else if (s.iter >= s.max_iter) s.done = kMaxIter;
+    else if (s.mixed && (s.since_ru >= s.ru_interval || rr < s.delta2 * s.rmax2)) s.done = kReliable;
   }
 };
 
@@ -400,24 +487,121 @@ struct WEpiResidual {
   }
 };
 
-// ---------------------------------------------------------------- small streaming kernels
+// Reliable update of the mixed recursion, in two launches:
+//   (1) FP64: s = b - M x_hi, the true residual of M x = b (where the cancellation happens), stored
+//       at the inner precision;
+//   (2) inner precision: r_lo = M^dagger s, |r_lo|^2 and the restart of the recursion.
+// The error of (2) is relative to the current residual (rounding of order eps_inner * cond(M)), the
+// same order as storing r_lo at the inner precision; convergence is only declared after the full FP64
+// residual of the normal equations (WEpiResidual) confirms it.
 template <class FieldT>
-__global__ void __launch_bounds__(kBlock) w_p_kernel(int V, FieldT r, FieldT p, CgScalars* sc, double* partials) {
+struct WEpiSysResidual {
+  static constexpr int NV = 0;
+  WField<QCD_PREC_DOUBLE> x, b;
+  FieldT s_lo;
+  double kappa;
+  __device__ __forceinline__ bool skip() const { return false; }
+  template <class A>
+  __device__ __forceinline__ void site(int i, spinor<double>& acc, A*) const {
+    using T = typename FieldT::T;
+    const spinor<double> mx = m_combine<WField<QCD_PREC_DOUBLE>, false>(x, i, acc, kappa);
+    const spinor<double> bv = b.load(i);
+    spinor<T> sv;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        sv.s[u].c[a] = {(T)(bv.s[u].c[a].re - mx.s[u].c[a].re), (T)(bv.s[u].c[a].im - mx.s[u].c[a].im)};
+    s_lo.store(i, sv);
+  }
+  template <class A>
+  __device__ __forceinline__ void finish(A*) const {}
+};
+
+template <class FieldT>
+struct WEpiReliableInner {
+  static constexpr int NV = 1;
+  FieldT s, r_lo;
+  double kappa;
+  CgScalars* sc;
+  double* partials;
+  __device__ __forceinline__ bool skip() const { return false; }
+  template <class T, class A>
+  __device__ __forceinline__ void site(int i, spinor<T>& acc, A* red) const {
+    const spinor<T> v = m_combine<FieldT, true>(s, i, acc, (T)kappa);
+    r_lo.store(i, v);
+    accum(red[0], norm2(v));
+  }
+  template <class A>
+  __device__ __forceinline__ void finish(A* red) const {
+    double v[1] = {(double)red[0]}, tot[1];
+    if (grid_sum_last_block<1>(v, partials, &sc->counter[4], tot) && threadIdx.x == 0) {
+      const double rr = tot[0];
+      if (!isfinite(rr)) { sc->done = kBreakdown; return; }
+      sc->beta = sc->iter > 0 ? rr / sc->rr_prev : 0.0;
+      sc->rr = rr;
+      sc->rmax2 = rr;
+      sc->since_ru = 0;
+      sc->ru_count += 1;
+      // below the tolerance: hand over to the full FP64 check (kConverged), never stop here
+      if (rr < sc->delit) sc->done = kConverged;
+      else if (sc->iter >= sc->max_iter) sc->done = kMaxIter;
+      else sc->done = kRunning;
+    }
+  }
+};
+
+// ---------------------------------------------------------------- small streaming kernels
+// p_r = r_r + beta_r p_r for every running RHS (grid.y = RHS)
+template <class FieldT>
+__global__ void __launch_bounds__(kBlock) w_p_kernel(int V, FieldT r_all, FieldT p_all, const CgScalars* sc) {
   using T = typename FieldT::T;
-  if (sc->done != kRunning) return;
-  const T beta = (T)sc->beta;
+  const int q = blockIdx.y;
+  if (sc[q].done != kRunning) return;
+  const T beta = (T)sc[q].beta;
+  const FieldT r = r_all.at(q), p = p_all.at(q);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
     const spinor<T> rv = r.load(i);
     spinor<T> pv = p.load(i);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        pv.s[q].c[a].re = fma(beta, pv.s[q].c[a].re, rv.s[q].c[a].re);
-        pv.s[q].c[a].im = fma(beta, pv.s[q].c[a].im, rv.s[q].c[a].im);
+        pv.s[u].c[a].re = fma(beta, pv.s[u].c[a].re, rv.s[u].c[a].re);
+        pv.s[u].c[a].im = fma(beta, pv.s[u].c[a].im, rv.s[u].c[a].im);
       }
     p.store(i, pv);
   }
+}
+
+// Start-up of one RHS with x = 0: r = rhs (inner precision), p = 0, x_lo = 0, x_hi = 0 and
+// sc->res2 = |rhs|^2 (the residual of the normal equations at x = 0 needs no operator).
+template <class FieldT, class XFieldT>
+__global__ void __launch_bounds__(kBlock) w_start_kernel(int V, WField<QCD_PREC_DOUBLE> rhs, FieldT r, FieldT p,
+                                                         XFieldT x_lo, WField<QCD_PREC_DOUBLE> x_hi, CgScalars* sc,
+                                                         double* partials) {
+  using T = typename FieldT::T;
+  double red[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+    const spinor<double> b = rhs.load(i);
+    spinor<T> rl, z;
+    spinor<typename XFieldT::T> zx;
+    spinor<double> zh;
+    zero(z);
+    zero(zx);
+    zero(zh);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) rl.s[u].c[a] = {(T)b.s[u].c[a].re, (T)b.s[u].c[a].im};
+    r.store(i, rl);
+    p.store(i, z);
+    x_lo.store(i, zx);
+    x_hi.store(i, zh);
+    red[0] += norm2(b);
+  }
+  double tot[1];
+  if (grid_sum_last_block<1>(red, partials, &sc->counter[4], tot) && threadIdx.x == 0) sc->res2 = tot[0];
 }
 
 // canonical complex128[V][4][3] <-> packed
@@ -490,34 +674,39 @@ __global__ void w_pack_links_kernel(Geom g, int V, const double2* __restrict__ c
 }
 
 // ---------------------------------------------------------------- host side
+// Workspace of an R-RHS CGNR: every per-RHS field is R fields back to back.
 struct WWork {
-  CgScalars* sc;
-  double* partials;
-  void *rhs, *x_hi, *t64;  // FP64
-  void *r, *p, *t;         // inner precision
-  void* x_lo;              // inner precision (aliases x_hi in FP64)
+  CgScalars* sc;           // [R]
+  double* partials;        // [max(R, 2)][kMaxPartials]
+  void *b64, *rhs, *x_hi;  // FP64, R fields each: b, M^dagger b, the solution accumulator
+  void* t64;               // FP64 scratch, one field (reliable updates run one RHS at a time)
+  void *r, *p, *t;         // inner precision, R fields each
+  void* x_lo;              // inner precision, R fields (aliases x_hi in FP64)
   size_t total;
 };
 
-static WWork w_carve(long long V, int prec, char* base) {
+static WWork w_carve(long long V, int prec, int R, char* base) {
   WWork w{};
   size_t off = 0;
   auto take = [&](size_t n) { void* q = base ? base + off : nullptr; off += align256(n); return q; };
-  w.sc = (CgScalars*)take(sizeof(CgScalars));
-  w.partials = (double*)take(sizeof(double) * kMaxPartials * 2);
+  w.sc = (CgScalars*)take(sizeof(CgScalars) * R);
+  w.partials = (double*)take(sizeof(double) * kMaxPartials * (R > 2 ? R : 2));
   const size_t f64 = wfield_bytes(QCD_PREC_DOUBLE, V), fin = wfield_bytes(prec, V);
-  w.rhs = take(f64);
-  w.x_hi = take(f64);
+  w.b64 = take(f64 * R);
+  w.rhs = take(f64 * R);
+  w.x_hi = take(f64 * R);
   w.t64 = take(f64);
-  w.r = take(fin);
-  w.p = take(fin);
-  w.t = take(fin);
-  w.x_lo = prec == QCD_PREC_DOUBLE ? w.x_hi : take(fin);
+  w.r = take(fin * R);
+  w.p = take(fin * R);
+  w.t = take(fin * R);
+  w.x_lo = prec == QCD_PREC_DOUBLE ? w.x_hi : take(fin * R);
   w.total = off;
   return w;
 }
 
-size_t wilson_workspace_bytes(const qcd_lattice* lat, int prec) { return w_carve(lat->V, prec, nullptr).total; }
+size_t wilson_workspace_bytes(const qcd_lattice* lat, int prec, int nrhs) {
+  return w_carve(lat->V, prec, nrhs, nullptr).total;
+}
 
 template <int PREC>
 static WField<PREC> wf(void* p, int V) {
@@ -578,113 +767,268 @@ int launch_wilson_op(const qcd_lattice* lat, void* out, const void* in, double k
   return QCD_ERR_UNSUPPORTED;
 }
 
-template <int PREC>
-static int wilson_cgnr_typed(qcd_lattice* lat, void* x, const void* b, double kappa, double tol, int max_iter,
+// (x, y) grid for a multi-RHS kernel: gy rows, x-extent within one wave of resident blocks (each
+// block ends in a fence + counter update, so further waves only add that cost).
+template <class KernelT>
+static dim3 w_grid(KernelT kernel, long long V, int gy) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  const long long need = (V + kBlock - 1) / kBlock;
+  long long gx = (long long)sms * per_sm / gy;
+  if (gx > need) gx = need;
+  if (gx > kMaxPartials) gx = kMaxPartials;
+  return dim3((unsigned)(gx > 0 ? gx : 1), (unsigned)gy);
+}
+
+// register block of right-hand sides: the opts value if given (1, 2, 4 in FP32; 1, 2 in FP64), else
+// 2 in FP32 (128 registers, two blocks per SM; 4 needs about 250) and 1 in FP64 (2 spills)
+int wilson_rhs_block(int prec, int R, int requested) {
+  const int cap = prec == QCD_PREC_DOUBLE ? 2 : 4;
+  if (requested > 0) return (requested == 1 || requested == 2 || requested == 4) && requested <= cap ? requested : -1;
+  const int def = prec == QCD_PREC_DOUBLE ? 1 : 2;
+  return R < def ? R : def;
+}
+
+template <int PREC, int RB>
+static int wilson_op_mrhs_typed(const qcd_lattice* lat, void* out, const void* in, int R, double kappa, int mode,
+                                cudaStream_t st) {
+  using FT = WField<PREC>;
+  const Geom g = make_geom(lat);
+  const int V = (int)lat->V;
+  auto U = wl<PREC>(lat->wilson_links[PREC], V);
+  const FT fin = wf<PREC>(const_cast<void*>(in), V), fout = wf<PREC>(out, V);
+  const int gy = (R + RB - 1) / RB;
+  if (mode == 0) {
+    auto k = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RB, WOpM<FT, 0>>;
+    k<<<w_grid(k, V, gy), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 0>{fin, fout, kappa, nullptr});
+  } else if (mode == 1) {
+    auto k = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RB, WOpM<FT, 1>>;
+    k<<<w_grid(k, V, gy), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 1>{fin, fout, kappa, nullptr});
+  } else {
+    auto k = wilson_mrhs_kernel<WLinks<PREC>, FT, true, RB, WOpM<FT, 2>>;
+    k<<<w_grid(k, V, gy), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 2>{fin, fout, kappa, nullptr});
+  }
+  QCD_CUDA(cudaGetLastError());
+  return QCD_OK;
+}
+
+int launch_wilson_op_mrhs(const qcd_lattice* lat, void* out, const void* in, int R, double kappa, int mode, int prec,
+                          cudaStream_t st) {
+  // the default register blocks: 1 in FP64, 2 in FP32 (1 for a single RHS)
+  if (prec == QCD_PREC_DOUBLE) return wilson_op_mrhs_typed<QCD_PREC_DOUBLE, 1>(lat, out, in, R, kappa, mode, st);
+  if (prec == QCD_PREC_SINGLE) {
+    if (wilson_rhs_block(prec, R, 0) == 1) return wilson_op_mrhs_typed<QCD_PREC_SINGLE, 1>(lat, out, in, R, kappa, mode, st);
+    return wilson_op_mrhs_typed<QCD_PREC_SINGLE, 2>(lat, out, in, R, kappa, mode, st);
+  }
+  return QCD_ERR_UNSUPPORTED;
+}
+
+// CGNR on R right-hand sides: each RHS r has its own scalars sc[r]; one iteration is
+//   K3  p_r = r_r + beta_r p_r                          (w_p_kernel, grid.y = RHS)
+//   K1  t_r = M p_r, alpha_r = rr_r / |t_r|^2             (multi-RHS operator kernel)
+//   K2  r_r -= alpha_r M^dagger t_r, x_r += alpha_r p_r, beta_r, exit tests
+// A converged or max-iteration RHS drops out of the kernels. Reliable updates (the true residual
+// s = b - M x_hi in FP64, then r_lo = M^dagger s at the inner precision) run per RHS between
+// iterations; a RHS whose residual falls below the tolerance is confirmed by the full FP64 residual
+// of the normal equations, M^dagger b - M^dagger M x_hi, before it stops. The host reads the R
+// states after every k iterations (k = opts->check_interval for one RHS, 1 for several, so that a
+// RHS waiting for its update does not idle while the others iterate).
+template <int PREC, int RB>
+static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, double kappa, double tol, int max_iter,
                              const qcd_solver_opts& o, void* ws, qcd_solve_info* info, cudaStream_t st) {
   using FT = WField<PREC>;
   using F64 = WField<QCD_PREC_DOUBLE>;
   const Geom g = make_geom(lat);
   const int V = (int)lat->V;
   const bool mixed = PREC != QCD_PREC_DOUBLE;
-  WWork w = w_carve(V, PREC, (char*)ws);
+  WWork w = w_carve(V, PREC, R, (char*)ws);
   auto U = wl<PREC>(lat->wilson_links[PREC], V);
   auto U64 = wl<QCD_PREC_DOUBLE>(lat->wilson_links[QCD_PREC_DOUBLE], V);
-  FT r = wf<PREC>(w.r, V), p = wf<PREC>(w.p, V), t = wf<PREC>(w.t, V), xl = wf<PREC>(w.x_lo, V);
-  F64 rhs = wf<QCD_PREC_DOUBLE>(w.rhs, V), xh = wf<QCD_PREC_DOUBLE>(w.x_hi, V), t64 = wf<QCD_PREC_DOUBLE>(w.t64, V);
-  const int grid = one_wave_grid(V, wilson_kernel<WLinks<PREC>, FT, true, WEpiUpdate<FT, FT>>);
+  const FT r = wf<PREC>(w.r, V), p = wf<PREC>(w.p, V), t = wf<PREC>(w.t, V), xl = wf<PREC>(w.x_lo, V);
+  const F64 b64 = wf<QCD_PREC_DOUBLE>(w.b64, V), rhs = wf<QCD_PREC_DOUBLE>(w.rhs, V);
+  const F64 xh = wf<QCD_PREC_DOUBLE>(w.x_hi, V), t64 = wf<QCD_PREC_DOUBLE>(w.t64, V);
+  const int grid = one_wave_grid(V, wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true, WEpiResidual<FT, false>>);
+  const int grid_ru = one_wave_grid(V, wilson_kernel<WLinks<PREC>, FT, true, WEpiReliableInner<FT>>);
+  const int gy = (R + RB - 1) / RB;
+  auto K1 = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RB, WEpiT<FT>>;
+  auto K2 = wilson_mrhs_kernel<WLinks<PREC>, FT, true, RB, WEpiUpdate<FT, FT>>;
+  const dim3 gp = w_grid(w_p_kernel<FT>, V, R), g1 = w_grid(K1, V, gy), g2 = w_grid(K2, V, gy);
+  const size_t cbytes = (size_t)V * 12 * sizeof(double2);  // one canonical spinor field
   long long launches = 0;
 
-  CgScalars h{};
-  h.tol2 = tol * tol;
-  h.max_iter = max_iter;
-  h.ru_interval = o.reliable_interval > 0 ? o.reliable_interval : 100;
-  h.delta2 = o.reliable_delta * o.reliable_delta;
-  h.mixed = mixed ? 1 : 0;
-  QCD_CUDA(cudaMemcpyAsync(w.sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, st));
-  // rhs = M^dagger b (FP64), x = 0, p = 0, r = rhs (the residual epilogue with t = b: rhs - M^dagger(0))
-  int rc = launch_wilson_pack(lat, w.t64, b, QCD_PREC_DOUBLE, false, st);
+  std::vector<CgScalars> h(R);
+  for (auto& s : h) {
+    s = CgScalars{};
+    s.tol2 = tol * tol;
+    s.max_iter = max_iter;
+    s.ru_interval = o.reliable_interval > 0 ? o.reliable_interval : 100;
+    s.delta2 = o.reliable_delta * o.reliable_delta;
+    s.mixed = mixed ? 1 : 0;
+  }
+  auto upload = [&]() -> int {
+    QCD_CUDA(cudaMemcpyAsync(w.sc, h.data(), sizeof(CgScalars) * R, cudaMemcpyHostToDevice, st));
+    return QCD_OK;
+  };
+  auto download = [&]() -> int {
+    QCD_CUDA(cudaMemcpyAsync(h.data(), w.sc, sizeof(CgScalars) * R, cudaMemcpyDeviceToHost, st));
+    QCD_CUDA(cudaStreamSynchronize(st));
+    return QCD_OK;
+  };
+  int rc = upload();
   if (rc) return rc;
-  wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true><<<grid, kBlock, 0, st>>>(g, V, U64, t64, WApplyM<F64, true>{t64, rhs, kappa});
-  w_zero_kernel<<<grid, kBlock, 0, st>>>(V, xh);
-  if (mixed) w_zero_kernel<<<grid, kBlock, 0, st>>>(V, xl);
-  w_zero_kernel<<<grid, kBlock, 0, st>>>(V, p);
-  w_zero_kernel<<<grid, kBlock, 0, st>>>(V, t64);
-  // r = rhs - M^dagger M x with x = 0: the residual kernel on t64 = 0 gives rhs; sets rr, delit
-  wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true><<<grid, kBlock, 0, st>>>(
-      g, V, U64, t64, WEpiResidual<FT, false>{t64, rhs, r, kappa, w.sc, w.partials});
+  // start-up per RHS: rhs_q = M^dagger b_q (FP64); r_q = rhs_q, p_q = x_q = 0; |rhs_q|^2
+  for (int q = 0; q < R; ++q) {
+    if ((rc = launch_wilson_pack(lat, b64.at(q).p, (const char*)b + q * cbytes, QCD_PREC_DOUBLE, false, st))) return rc;
+    wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true><<<grid, kBlock, 0, st>>>(
+        g, V, U64, b64.at(q), WApplyM<F64, true>{b64.at(q), rhs.at(q), kappa});
+    w_start_kernel<<<grid, kBlock, 0, st>>>(V, rhs.at(q), r.at(q), p.at(q), xl.at(q), xh.at(q), w.sc + q, w.partials);
+    launches += 3;
+  }
   QCD_CUDA(cudaGetLastError());
-  launches += 6 + (mixed ? 1 : 0);
-  QCD_CUDA(cudaMemcpyAsync(&h, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-  QCD_CUDA(cudaStreamSynchronize(st));
-  const double rhs2 = h.res2;
-  h.delit = tol * tol * rhs2;
-  h.rr = h.rr_prev = h.rmax2 = rhs2;
-  h.beta = 0.0;
-  h.iter = 0;
-  h.ru_count = 0;
-  h.done = !std::isfinite(rhs2) ? kBreakdown : (rhs2 == 0.0 ? kTrueConverged : kRunning);
-  QCD_CUDA(cudaMemcpyAsync(w.sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, st));
+  if ((rc = download())) return rc;
+  std::vector<double> rhs2(R);
+  for (int q = 0; q < R; ++q) {
+    CgScalars& s = h[q];
+    rhs2[q] = s.res2;
+    s.delit = tol * tol * rhs2[q];
+    s.rr = s.rr_prev = s.rmax2 = rhs2[q];
+    s.done = !std::isfinite(rhs2[q]) ? kBreakdown : (rhs2[q] == 0.0 ? kTrueConverged : kRunning);
+  }
+  if ((rc = upload())) return rc;
 
-  auto true_residual = [&](bool final_report) -> int {
-    // x_hi += x_lo; t64 = M x_hi; res = rhs - M^dagger t64
-    if (mixed) w_accumulate_kernel<<<grid, kBlock, 0, st>>>(V, xh, xl);
-    wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, false><<<grid, kBlock, 0, st>>>(g, V, U64, xh, WApplyM<F64, false>{xh, t64, kappa});
+  // FP64 residual of the normal equations for RHS q: x_hi += x_lo; t64 = M x_hi;
+  // res = rhs - M^dagger t64 (-> r_lo unless final_report); sc[q] state from |res|^2
+  auto true_residual = [&](int q, bool final_report) -> int {
+    if (mixed) w_accumulate_kernel<<<grid, kBlock, 0, st>>>(V, xh.at(q), xl.at(q));
+    wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, false><<<grid, kBlock, 0, st>>>(
+        g, V, U64, xh.at(q), WApplyM<F64, false>{xh.at(q), t64, kappa});
     if (final_report)
       wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true><<<grid, kBlock, 0, st>>>(
-          g, V, U64, t64, WEpiResidual<FT, true>{t64, rhs, r, kappa, w.sc, w.partials});
+          g, V, U64, t64, WEpiResidual<FT, true>{t64, rhs.at(q), r.at(q), kappa, w.sc + q, w.partials});
     else
       wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true><<<grid, kBlock, 0, st>>>(
-          g, V, U64, t64, WEpiResidual<FT, false>{t64, rhs, r, kappa, w.sc, w.partials});
+          g, V, U64, t64, WEpiResidual<FT, false>{t64, rhs.at(q), r.at(q), kappa, w.sc + q, w.partials});
     launches += mixed ? 3 : 2;
     QCD_CUDA(cudaGetLastError());
     return QCD_OK;
   };
 
-  const int k = o.check_interval > 0 ? o.check_interval : 8;
-  int status = QCD_OK;
+  // reliable update of the mixed recursion for RHS q (x_hi += x_lo; s = b - M x_hi in FP64;
+  // r_lo = M^dagger s at the inner precision)
+  auto reliable_update = [&](int q) -> int {
+    w_accumulate_kernel<<<grid, kBlock, 0, st>>>(V, xh.at(q), xl.at(q));
+    wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, false><<<grid, kBlock, 0, st>>>(
+        g, V, U64, xh.at(q), WEpiSysResidual<FT>{xh.at(q), b64.at(q), t.at(q), kappa});
+    wilson_kernel<WLinks<PREC>, FT, true><<<grid_ru, kBlock, 0, st>>>(
+        g, V, U, t.at(q), WEpiReliableInner<FT>{t.at(q), r.at(q), kappa, w.sc + q, w.partials});
+    launches += 3;
+    QCD_CUDA(cudaGetLastError());
+    return QCD_OK;
+  };
+
+  const bool profile = o.profile != 0;
+  const int k = R > 1 ? 1 : (o.check_interval > 0 ? o.check_interval : 8);
+  std::vector<cudaEvent_t> ev(profile ? 2 * k : 0, nullptr);
+  auto cleanup = [&]() {
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { cleanup(); return cuda_fail(cudaGetLastError(), "cudaEventCreate"); }
+  double dslash_ms = 0.0;
+  long long op_launches = 0;
   while (true) {
-    if (h.done == kBreakdown) { status = QCD_ERR_BREAKDOWN; break; }
-    if (h.done == kMaxIter) { status = QCD_ERR_NOT_CONVERGED; break; }
-    if (h.done == kTrueConverged) break;
-    if (h.done == kConverged || (mixed && h.done == kReliable)) {
-      if ((rc = true_residual(false))) return rc;
-    } else {
-      for (int i = 0; i < k; ++i) {
-        w_p_kernel<<<grid, kBlock, 0, st>>>(V, r, p, w.sc, w.partials);
-        wilson_kernel<WLinks<PREC>, FT, false><<<grid, kBlock, 0, st>>>(g, V, U, p, WEpiT<FT>{p, t, kappa, w.sc, w.partials});
-        wilson_kernel<WLinks<PREC>, FT, true><<<grid, kBlock, 0, st>>>(
-            g, V, U, t, WEpiUpdate<FT, FT>{t, p, r, xl, kappa, w.sc, w.partials});
-        launches += 3;
+    bool running = false, updated = false;
+    for (int q = 0; q < R; ++q) {
+      const int d = h[q].done;
+      if (d == kConverged) {  // confirmed (or refuted) by the full FP64 residual
+        if ((rc = true_residual(q, false))) { cleanup(); return rc; }
+        updated = true;
+      } else if (mixed && d == kReliable) {
+        if ((rc = reliable_update(q))) { cleanup(); return rc; }
+        updated = true;
+      } else if (d == kRunning) {
+        running = true;
       }
-      QCD_CUDA(cudaGetLastError());
     }
-    QCD_CUDA(cudaMemcpyAsync(&h, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-    QCD_CUDA(cudaStreamSynchronize(st));
+    if (updated) {
+      if ((rc = download())) { cleanup(); return rc; }
+      continue;
+    }
+    if (!running) break;
+    for (int i = 0; i < k; ++i) {
+      w_p_kernel<<<gp, kBlock, 0, st>>>(V, r, p, w.sc);
+      if (profile) cudaEventRecord(ev[2 * i], st);
+      K1<<<g1, kBlock, 0, st>>>(g, V, U, p, R, WEpiT<FT>{p, t, kappa, w.sc, w.partials});
+      K2<<<g2, kBlock, 0, st>>>(g, V, U, t, R, WEpiUpdate<FT, FT>{t, p, r, xl, kappa, w.sc, w.partials});
+      if (profile) cudaEventRecord(ev[2 * i + 1], st);
+      launches += 3;
+      op_launches += 2;
+    }
+    QCD_CUDA(cudaGetLastError());
+    if ((rc = download())) { cleanup(); return rc; }
+    if (profile) {
+      for (int i = 0; i < k; ++i) {
+        float ms = 0.f;
+        const cudaError_t e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "cudaEventElapsedTime"); }
+        dslash_ms += ms;
+      }
+    }
   }
-  // final: FP64 residual of the normal equations, and x out
-  if ((rc = true_residual(true))) return rc;
-  if ((rc = launch_wilson_pack(lat, w.x_hi, x, QCD_PREC_DOUBLE, true, st))) return rc;
-  QCD_CUDA(cudaMemcpyAsync(&h, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-  QCD_CUDA(cudaStreamSynchronize(st));
-  const double true_rel = rhs2 > 0 ? std::sqrt(h.res2 / rhs2) : 0.0;
-  if (status == QCD_OK && !(true_rel <= tol)) status = QCD_ERR_NOT_CONVERGED;
+  cleanup();
+  // final report: a RHS that ended on a confirmed FP64 residual (kTrueConverged) already holds it
+  // in res2 with x_lo folded into x_hi; the others are recomputed here
+  for (int q = 0; q < R; ++q)
+    if (h[q].done != kTrueConverged && (rc = true_residual(q, true))) return rc;
+  for (int q = 0; q < R; ++q)
+    if ((rc = launch_wilson_pack(lat, xh.at(q).p, (char*)x + q * cbytes, QCD_PREC_DOUBLE, true, st))) return rc;
+  launches += R;
+  if ((rc = download())) return rc;
+  int status = QCD_OK;
+  for (int q = 0; q < R; ++q) {
+    const CgScalars& s = h[q];
+    const double true_rel = rhs2[q] > 0 ? std::sqrt(s.res2 / rhs2[q]) : 0.0;
+    int st_q = s.done == kBreakdown ? QCD_ERR_BREAKDOWN
+                                    : (s.done == kMaxIter ? QCD_ERR_NOT_CONVERGED : QCD_OK);
+    if (st_q == QCD_OK && !(true_rel <= tol)) st_q = QCD_ERR_NOT_CONVERGED;
+    if (st_q == QCD_ERR_BREAKDOWN || (status == QCD_OK && st_q != QCD_OK)) status = st_q;
+    if (info) {
+      qcd_solve_info& in = info[q];
+      in.iterations = s.iter;
+      in.reliable_updates = s.ru_count;
+      in.true_rel_residual = true_rel;
+      in.iterated_rel_residual = rhs2[q] > 0 ? std::sqrt(s.rr / rhs2[q]) : 0.0;
+      in.converged = st_q == QCD_OK;
+      in.status = st_q;
+    }
+  }
   if (info) {
-    info->iterations = h.iter;
-    info->reliable_updates = h.ru_count;
-    info->true_rel_residual = true_rel;
-    info->iterated_rel_residual = rhs2 > 0 ? std::sqrt(h.rr / rhs2) : 0.0;
-    info->converged = status == QCD_OK;
-    info->status = status;
-    info->kernel_launches = (int)launches;
-    info->dslash_launches = 2 * h.iter;
+    info[0].kernel_launches = (int)launches;
+    info[0].dslash_launches = (int)op_launches;
+    info[0].dslash_ms = dslash_ms;
   }
   return status;
 }
 
-int run_wilson_cgnr(qcd_lattice* lat, void* x, const void* b, double kappa, double tol, int max_iter,
+int run_wilson_cgnr(qcd_lattice* lat, int R, void* x, const void* b, double kappa, double tol, int max_iter,
                     const qcd_solver_opts& o, void* ws, qcd_solve_info* info, cudaStream_t st) {
-  if (o.prec_inner == QCD_PREC_DOUBLE) return wilson_cgnr_typed<QCD_PREC_DOUBLE>(lat, x, b, kappa, tol, max_iter, o, ws, info, st);
-  if (o.prec_inner == QCD_PREC_SINGLE) return wilson_cgnr_typed<QCD_PREC_SINGLE>(lat, x, b, kappa, tol, max_iter, o, ws, info, st);
+  const int rb = wilson_rhs_block(o.prec_inner, R, o.rhs_block);
+  if (rb < 1) {
+    set_error("unsupported RHS block %d for Wilson precision %d", o.rhs_block, o.prec_inner);
+    return QCD_ERR_INVALID_ARG;
+  }
+  if (o.prec_inner == QCD_PREC_DOUBLE) {
+    if (rb == 1) return wilson_cgnr_typed<QCD_PREC_DOUBLE, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+    return wilson_cgnr_typed<QCD_PREC_DOUBLE, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+  }
+  if (o.prec_inner == QCD_PREC_SINGLE) {
+    if (rb == 1) return wilson_cgnr_typed<QCD_PREC_SINGLE, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+    if (rb == 2) return wilson_cgnr_typed<QCD_PREC_SINGLE, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+    return wilson_cgnr_typed<QCD_PREC_SINGLE, 4>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+  }
   return QCD_ERR_UNSUPPORTED;
 }
 

@@ -110,9 +110,12 @@ SIGNATURES = {
     "qcd_wilson_pack_field": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qcd_wilson_unpack_field": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qcd_wilson_op": (_i, [_vp, _vp, _vp, _d, _i, _i, _vp]),
-    "qcd_wilson_workspace_bytes": (_sz, [_vp, ctypes.POINTER(qcd_solver_opts)]),
+    "qcd_wilson_op_mrhs": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _vp]),
+    "qcd_wilson_workspace_bytes": (_sz, [_vp, ctypes.POINTER(qcd_solver_opts), _i]),
     "qcd_wilson_cgnr": (_i, [_vp, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp,
                              ctypes.POINTER(qcd_solve_info), _vp]),
+    "qcd_wilson_cgnr_mrhs": (_i, [_vp, _i, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp,
+                                  ctypes.POINTER(qcd_solve_info), _vp]),
     "qcd_tune_mrhs": (_i, [_vp, _i, _vp, _vp, _d, ctypes.POINTER(qcd_solver_opts), _vp, ctypes.c_char_p,
                            ctypes.POINTER(_i), _vp]),
     "qcd_tune_batched": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
@@ -339,8 +342,13 @@ def qcd_wilson_op(lat, out_dev, in_dev, kappa, op, prec, stream=None):
                   "qcd_wilson_op")
 
 
-def qcd_wilson_workspace_bytes(lat, opts=None) -> int:
-    return _lib.qcd_wilson_workspace_bytes(lat, ctypes.byref(opts) if opts is not None else None)
+def qcd_wilson_op_mrhs(lat, out_dev, in_dev, nrhs, kappa, op, prec, stream=None):
+    return _check(_lib.qcd_wilson_op_mrhs(lat, _ptr(out_dev), _ptr(in_dev), int(nrhs), float(kappa), int(op), prec,
+                                          _stream(stream)), "qcd_wilson_op_mrhs")
+
+
+def qcd_wilson_workspace_bytes(lat, opts=None, nrhs=1) -> int:
+    return _lib.qcd_wilson_workspace_bytes(lat, ctypes.byref(opts) if opts is not None else None, int(nrhs))
 
 
 def qcd_wilson_cgnr(lat, x_dev, b_dev, kappa, tol, max_iter, opts, workspace_dev, stream=None,
@@ -352,6 +360,18 @@ def qcd_wilson_cgnr(lat, x_dev, b_dev, kappa, tol, max_iter, opts, workspace_dev
     if rc in raise_on:
         _check(rc, "qcd_wilson_cgnr")
     return rc, info.as_dict()
+
+
+def qcd_wilson_cgnr_mrhs(lat, nrhs, x_dev, b_dev, kappa, tol, max_iter, opts, workspace_dev, stream=None,
+                         raise_on=(QCD_ERR_INVALID_ARG, QCD_ERR_CUDA, QCD_ERR_UNSUPPORTED, QCD_ERR_NO_LINKS)):
+    """Returns (status, [info dict per RHS])."""
+    infos = (qcd_solve_info * max(int(nrhs), 1))()
+    rc = _lib.qcd_wilson_cgnr_mrhs(lat, int(nrhs), _ptr(x_dev), _ptr(b_dev), float(kappa), float(tol), int(max_iter),
+                                   ctypes.byref(opts) if opts is not None else None, _ptr(workspace_dev), infos,
+                                   _stream(stream))
+    if rc in raise_on:
+        _check(rc, "qcd_wilson_cgnr_mrhs")
+    return rc, [i.as_dict() for i in infos]
 
 
 def qcd_tune_mrhs(lat, nrhs, x_dev, b_dev, mass, opts, workspace_dev, cache_path=None, stream=None) -> int:

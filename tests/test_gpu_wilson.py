@@ -149,3 +149,159 @@ def test_wilson_full_size_32c64(H):
         assert H.rel(got[sites], W.dslash_w_sites(U, b, dims, sites)) <= TOL[prec]
     rc, info, x = rig.cgnr(b, kappa, 1e-10, Q.QCD_PREC_SINGLE)
     assert rc == Q.QCD_OK and info["true_rel_residual"] <= 1e-10
+
+
+# ---------------------------------------------------------------- several right-hand sides
+def _spinors(dims, n, seed0=2):
+    return np.stack([I.make_spinor(dims, seed=seed0 + k) for k in range(n)])
+
+
+def _op_mrhs(rig, psis, kappa, op, prec):
+    import torch
+    n = len(psis)
+    fb = Q.qcd_wilson_field_bytes(rig.h, prec)
+    fin, fout = rig.lat.empty_bytes(n * fb), rig.lat.empty_bytes(n * fb)
+    for k in range(n):
+        Q.qcd_wilson_pack_field(rig.h, fin[k * fb:(k + 1) * fb], rig.H.dev(psis[k]), prec)
+    Q.qcd_wilson_op_mrhs(rig.h, fout, fin, n, kappa, op, prec)
+    out = []
+    for k in range(n):
+        o = torch.zeros((rig.V, 4, 3), dtype=torch.complex128, device="cuda")
+        Q.qcd_wilson_unpack_field(rig.h, o, fout[k * fb:(k + 1) * fb], prec)
+        out.append(rig.H.host(o))
+    return out
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 6, 8)])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 5])
+def test_wilson_op_mrhs_matches_oracle(H, dims, nrhs):
+    """Every RHS of the multi-RHS operator (ragged last register block included) against the oracle."""
+    U = I.make_links(dims, kind="haar", seed=1)
+    psis = _spinors(dims, nrhs, seed0=10)
+    rig = WRig(H, dims, U)
+    kappa = 0.13
+    for prec in (Q.QCD_PREC_DOUBLE, Q.QCD_PREC_SINGLE):
+        for op in (Q.QCD_WILSON_DSLASH, Q.QCD_WILSON_M, Q.QCD_WILSON_MDAG):
+            got = _op_mrhs(rig, psis, kappa, op, prec)
+            for k in range(nrhs):
+                f = {Q.QCD_WILSON_DSLASH: lambda v: W.dslash_w(U, v, dims),
+                     Q.QCD_WILSON_M: lambda v: W.apply_m(U, v, dims, kappa),
+                     Q.QCD_WILSON_MDAG: lambda v: W.apply_mdag(U, v, dims, kappa)}[op]
+                assert H.rel(got[k], f(psis[k])) <= TOL[prec], (prec, op, k)
+
+
+def _cgnr_mrhs(rig, bs, kappa, tol=1e-10, prec=Q.QCD_PREC_SINGLE, rhs_block=0, max_iter=10000):
+    torch = rig.torch
+    n = len(bs)
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner = prec
+    opts.rhs_block = rhs_block
+    ws = rig.lat.empty_bytes(Q.qcd_wilson_workspace_bytes(rig.h, opts, n))
+    bd = rig.H.dev(np.stack(bs))
+    x = torch.zeros_like(bd)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    rc, infos = Q.qcd_wilson_cgnr_mrhs(rig.h, n, x, bd, kappa, tol, max_iter, opts, ws, stream=s)
+    s.synchronize()
+    return rc, infos, rig.H.host(x)
+
+
+@pytest.mark.parametrize("prec,rhs_block", [(Q.QCD_PREC_SINGLE, 0), (Q.QCD_PREC_SINGLE, 1), (Q.QCD_PREC_SINGLE, 2),
+                                            (Q.QCD_PREC_SINGLE, 4), (Q.QCD_PREC_DOUBLE, 0), (Q.QCD_PREC_DOUBLE, 2)])
+def test_wilson_cgnr_mrhs_matches_oracle(H, prec, rhs_block):
+    dims, kappa = (4, 4, 4, 4), 0.125
+    U = I.make_links(dims, kind="haar", seed=1)
+    bs = list(_spinors(dims, 5))
+    rig = WRig(H, dims, U)
+    rc, infos, x = _cgnr_mrhs(rig, bs, kappa, 1e-10, prec, rhs_block)
+    assert rc == Q.QCD_OK, infos
+    for k, b in enumerate(bs):
+        assert infos[k]["converged"] and infos[k]["true_rel_residual"] <= 1e-10
+        rhs = W.apply_mdag(U, b, dims, kappa)
+        nres = rhs - W.apply_mdag(U, W.apply_m(U, x[k], dims, kappa), dims, kappa)
+        assert np.linalg.norm(nres) / np.linalg.norm(rhs) <= 1.01e-10
+        ref = W.cgnr(U, b, dims, kappa, tol=1e-12, max_iter=10000)
+        assert H.rel(x[k], ref["x"]) <= 1e-7
+        if prec == Q.QCD_PREC_SINGLE:
+            assert infos[k]["reliable_updates"] >= 1
+
+
+def test_wilson_cgnr_mrhs_each_rhs_stops_on_its_own(H):
+    """A zero RHS converges at once, a NaN RHS breaks down, the others still reach the tolerance."""
+    dims, kappa = (4, 2, 4, 6), 0.12
+    U = I.make_links(dims, kind="haar", seed=3)
+    bs = list(_spinors(dims, 4, seed0=20))
+    bs[1] = np.zeros_like(bs[1])
+    bs[2] = bs[2].copy()
+    bs[2][5, 0, 1] = np.nan
+    rig = WRig(H, dims, U)
+    rc, infos, x = _cgnr_mrhs(rig, bs, kappa)
+    assert rc == Q.QCD_ERR_BREAKDOWN
+    assert infos[1]["status"] == Q.QCD_OK and infos[1]["iterations"] == 0 and not np.any(x[1])
+    assert infos[2]["status"] == Q.QCD_ERR_BREAKDOWN
+    for k in (0, 3):
+        assert infos[k]["status"] == Q.QCD_OK and infos[k]["true_rel_residual"] <= 1e-10
+        ref = W.cgnr(U, bs[k], dims, kappa, tol=1e-12, max_iter=10000)
+        assert H.rel(x[k], ref["x"]) <= 1e-7
+    rc, infos, _ = _cgnr_mrhs(rig, [bs[0], bs[3]], kappa, max_iter=4)
+    assert rc == Q.QCD_ERR_NOT_CONVERGED and all(i["iterations"] == 4 for i in infos)
+
+
+def test_wilson_mrhs_argument_checks(H):
+    dims = (2, 2, 2, 2)
+    rig = WRig(H, dims, I.make_links(dims, kind="haar", seed=1))
+    opts = Q.qcd_solver_opts_default()
+    assert Q.qcd_wilson_workspace_bytes(rig.h, opts, 0) == 0
+    assert Q.qcd_wilson_workspace_bytes(rig.h, opts, 17) == 0
+    assert Q.qcd_wilson_workspace_bytes(rig.h, opts, 16) > Q.qcd_wilson_workspace_bytes(rig.h, opts, 1) > 0
+    b = [I.make_spinor(dims, seed=2)]
+    for prec, rb in ((Q.QCD_PREC_SINGLE, 3), (Q.QCD_PREC_SINGLE, 8), (Q.QCD_PREC_DOUBLE, 4)):
+        opts = Q.qcd_solver_opts_default()
+        opts.prec_inner, opts.rhs_block = prec, rb
+        ws = rig.lat.empty_bytes(Q.qcd_wilson_workspace_bytes(rig.h, Q.qcd_solver_opts_default(), 1))
+        bd = H.dev(np.stack(b))
+        x = rig.torch.zeros_like(bd)
+        rc, _ = Q.qcd_wilson_cgnr_mrhs(rig.h, 1, x, bd, 0.1, 1e-10, 100, opts, ws, raise_on=())
+        assert rc == Q.QCD_ERR_INVALID_ARG
+    rc, _ = Q.qcd_wilson_cgnr_mrhs(rig.h, 0, x, bd, 0.1, 1e-10, 100, None, ws, raise_on=())
+    assert rc == Q.QCD_ERR_INVALID_ARG
+
+
+def test_wilson_full_size_32c64_8rhs(H):
+    """32^3 x 64, kappa = 0.125, 8 right-hand sides in one mixed CGNR: every RHS to 1e-10 (FP64
+    residual), RHS 0 against its own single-RHS solve, and the normal-equation residual recomputed by
+    the oracle at sampled sites."""
+    import torch
+    dims, kappa = (32, 32, 32, 64), 0.125
+    U = I.make_links(dims, kind="haar", seed=1)
+    rig = WRig(H, dims, U)
+    bs = list(_spinors(dims, 8))
+    rc, infos, x = _cgnr_mrhs(rig, bs, kappa)
+    assert rc == Q.QCD_OK
+    assert all(i["converged"] and i["true_rel_residual"] <= 1e-10 for i in infos)
+    rc1, info1, x1 = rig.cgnr(bs[0], kappa, 1e-10, Q.QCD_PREC_SINGLE)
+    assert rc1 == Q.QCD_OK
+    assert H.rel(x[0], x1) <= 1e-8
+    # oracle: (M^dagger b - M^dagger M x) at sampled sites, relative to |M^dagger b| there
+    V = S.volume(dims)
+    rng = np.random.default_rng(7)
+    sites = rng.choice(V, 64, replace=False)
+    L = list(dims)
+    stride = [1, L[0], L[0] * L[1], L[0] * L[1] * L[2]]
+    for k in (0, 7):
+        near = set()
+        for s_ in sites:
+            c = [(s_ // stride[m]) % L[m] for m in range(4)]
+            near.add(int(s_))
+            for m in range(4):
+                for d in (1, -1):
+                    near.add(int(s_ + (((c[m] + d) % L[m]) - c[m]) * stride[m]))
+        near = np.array(sorted(near))
+        res = np.zeros_like(bs[k])          # b - M x on the sites next to the samples
+        res[near] = bs[k][near] - (x[k][near] - kappa * W.dslash_w_sites(U, x[k], dims, near))
+        g5r = W.gamma5(res)
+        nres = W.gamma5(g5r[sites] - kappa * W.dslash_w_sites(U, g5r, dims, sites))   # M^dagger (b - M x)
+        g5b = W.gamma5(bs[k])
+        rhs = W.gamma5(g5b[sites] - kappa * W.dslash_w_sites(U, g5b, dims, sites))
+        assert np.linalg.norm(nres) / np.linalg.norm(rhs) <= 1e-9
+    torch.cuda.empty_cache()
