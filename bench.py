@@ -61,6 +61,10 @@ WORKLOADS = {
                              inner="single18", nrhs=8,
                              desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, 8 RHS in one multi-RHS CGNR on M^dagger M: "
                                   "FP32 recursion with FP64 reliable updates, to 1e-10"),
+    "wilson24c48_single": dict(kind_solve="wilson", dims=(24, 24, 24, 48), kind="haar", kappa=0.125, tol=1e-10,
+                               inner="single18", nrhs=1,
+                               desc="Wilson 24^3x48 Haar SU(3), kappa=0.125, CGNR, FP32 recursion with FP64 reliable "
+                                    "updates, to 1e-10 (the small case for counter captures)"),
     "wilson32c64_single": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
                                inner="single18", nrhs=1,
                                desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion with "
@@ -124,30 +128,26 @@ def _clock_summary(proc, path):
             "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def kernel_source_sha() -> str:
-    """sha256 over the CUDA sources of the library (the ncu traffic figures are valid only for these)."""
-    import glob
+def sources_sha(files) -> str:
+    """sha256 over the listed CUDA sources of the library (ncu traffic figures hold only for these)."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1311_2719_gb300", "csrc", "*.cu*"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for f in sorted(files):
+        h.update(f.encode())
+        with open(os.path.join(ROOT, "paper_1311_2719_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
 def ncu_traffic(workload):
     """DRAM bytes per operator launch (mean of K1 and K2) from profiles/ncu_traffic.json, or None when
-    the file is absent or was taken on different kernel sources."""
+    the file has no entry for the workload or the entry was taken on other kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
-            d = json.load(fh)
-    except (OSError, ValueError):
-        return None
-    if d.get("source_sha256") != kernel_source_sha():
-        return None
-    w = d.get("workloads", {}).get(workload)
-    if not w:
+            w = json.load(fh).get("workloads", {}).get(workload)
+        if not w or w.get("sources_sha256") != sources_sha(w["sources"]):
+            return None
+    except (OSError, ValueError, KeyError):
         return None
     return (w["K1_bytes"] + w["K2_bytes"]) / 2
 
@@ -547,10 +547,7 @@ def run_gpu_wilson(args, wl):
     x_host = torch.empty_like(b_host).pin_memory()
     bufs = {p: lat.empty_bytes(Q.qcd_wilson_links_bytes(lat.handle, p)) for p in (0, 1)}
     opts = Q.qcd_solver_opts_default()
-    ws = {}
-    for p in (0, 1):
-        opts.prec_inner = p
-        ws[p] = lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))
+    ws = {1: lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))}  # FP32 inner (the default)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     launches_links = 2
 
@@ -605,6 +602,9 @@ def run_gpu_wilson(args, wl):
         dist.barrier()
     ms_prof, runs_prof = timed(1, max(1, min(args.steps, 3)), profile=True)
     ms_e2e, runs_e2e = timed(1, args.steps, host_io=True)
+    del ws[1]
+    opts.prec_inner = 0
+    ws[0] = lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))
     solve(0)
     ms64, runs64 = timed(0, max(1, min(args.steps, 2)))
 
@@ -680,7 +680,7 @@ def run_gpu_wilson(args, wl):
         "roofline": {"bound": "hbm", "kernel": "wilson_mrhs_kernel (CGNR K1+K2 launches, FP32)",
                      "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
-                     "traffic": None, "alg_bytes_per_launch": round(alg / d_launches),
+                     "traffic": ncu_traffic(args.workload), "alg_bytes_per_launch": round(alg / d_launches),
                      "alg_bytes_per_site": {"links_per_launch": link_b, "k1_per_rhs": k1_b, "k2_per_rhs": k2_b},
                      "avg_launch_us": round(d_ms / d_launches * 1e3, 3)},
         "operator_alone": {

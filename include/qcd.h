@@ -271,8 +271,8 @@ QCD_API int qcd_wilson_unpack_field(const qcd_lattice* lat, void* canonical_dev,
 QCD_API int qcd_wilson_op(const qcd_lattice* lat, void* out_dev, const void* in_dev, double kappa, int op, int prec,
                   void* stream);
 /* The same operator on nrhs right-hand sides at once: nrhs packed fields back to back
- * (nrhs * qcd_wilson_field_bytes bytes each side); every link is loaded once per register block of
- * right-hand sides (2 in SINGLE, 1 in DOUBLE) and applied to all of them. 1 <= nrhs <= 16. */
+ * (nrhs * qcd_wilson_field_bytes bytes each side); one thread per site walks all nrhs right-hand
+ * sides, applying each loaded link to one RHS at a time. 1 <= nrhs <= 16. */
 QCD_API int qcd_wilson_op_mrhs(const qcd_lattice* lat, void* out_dev, const void* in_dev, int nrhs, double kappa,
                        int op, int prec, void* stream);
 /* Bytes of the device workspace qcd_wilson_cgnr (nrhs = 1) or qcd_wilson_cgnr_mrhs needs for these
@@ -290,8 +290,8 @@ QCD_API size_t qcd_wilson_workspace_bytes(const qcd_lattice* lat, const qcd_solv
 QCD_API int qcd_wilson_cgnr(qcd_lattice* lat, void* x_dev, const void* b_dev, double kappa, double tol, int max_iter,
                     const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream);
 /* nrhs independent CGNR solves on one lattice in one set of launches: each loaded link is applied to
- * a register block of right-hand sides (opts->rhs_block: 0 = 2 in SINGLE / 1 in DOUBLE; 1, 2, 4 in
- * SINGLE; 1, 2 in DOUBLE), each RHS keeps its own scalars, reliable updates and exit.
+ * a register block of right-hand sides (opts->rhs_block: 0 = 1; 1, 2, 4 in SINGLE; 1, 2 in
+ * DOUBLE), each RHS keeps its own scalars, reliable updates and exit.
  *   x_dev, b_dev  : nrhs canonical fields back to back, complex128[nrhs][V][4][3].
  *   workspace_dev : qcd_wilson_workspace_bytes(lat, opts, nrhs) bytes.
  *   info          : optional array of nrhs entries; the launch counters and, with opts->profile, the

@@ -228,10 +228,11 @@ __device__ __forceinline__ spinor<typename LinksT::T> wilson_hop(const Geom& g, 
   return acc;
 }
 
-// resident 128-thread blocks per SM: FP64 4 (at most 128 registers: 16 warps to hide the FP64
-// pipe's latency); FP32 none (0: the compiler's own choice, 80 registers without spills)
+// resident 128-thread blocks per SM: 4 (a cap of 128 registers). In FP64 that keeps 16 warps on
+// the FP64 pipe; in FP32 the compiler spends the registers above its own choice (80) on loads in
+// flight, which the latency-bound kernel needs more than a fifth and sixth block.
 template <typename T>
-struct WMinBlocks { static constexpr int value = sizeof(T) == 8 ? 4 : 0; };
+struct WMinBlocks { static constexpr int value = 4; };
 
 template <class LinksT, class FieldT, bool G5IN, class Epi>
 __global__ void __launch_bounds__(kBlock, WMinBlocks<typename LinksT::T>::value) wilson_kernel(Geom g, int V, LinksT U, FieldT in, Epi epi) {
@@ -292,49 +293,80 @@ struct WApplyM {  // out = M in or M^dagger in
   __device__ __forceinline__ void finish(A*) const {}
 };
 
+// resident 128-thread blocks per SM for a register block of RB right-hand sides (register caps
+// 128 for RB <= 2 and 170 for RB = 4 in FP32; 170 / 255 in FP64)
+template <typename T, int RB>
+struct WMrhsMinBlocks {
+  static constexpr int value = sizeof(T) == 8 ? (RB == 1 ? 3 : 2) : (RB <= 2 ? 4 : 3);
+};
+
 // ---------------------------------------------------------------- multi-RHS operator kernel
-// grid.y enumerates blocks of RB right-hand sides: each link is loaded once and applied to the RB
-// spinors of that block (fields of all RHS back to back, WField::at). The epilogue sees one
-// (site, RHS) pair at a time; reducing epilogues finish with one deterministic sum per RHS.
+// One thread per site (1-D grid, one wave). For its site a thread walks the right-hand sides in
+// register blocks of RB: each loaded link is applied to the RB spinors of a block, and the next
+// block reloads the same links (fields of all RHS back to back, WField::at). The epilogue sees one
+// (site, RHS) pair at a time; reducing epilogues keep per-thread, per-RHS partials in shared memory
+// and finish with one deterministic sum per RHS.
+// (Measured on 32^3x64 with 8 RHS, FP32: this layout with RB = 1 beats one grid row per register
+// block, whose rows each stream the links from DRAM, and one lane per register block, which spreads
+// a warp's neighbour gathers over the fields and thrashes L2.)
 template <class LinksT, class FieldT, bool G5IN, int RB, class Epi>
-__global__ void __launch_bounds__(kBlock) wilson_mrhs_kernel(Geom g, int V, LinksT U, FieldT in, int nrhs, Epi epi) {
+__global__ void __launch_bounds__(kBlock, WMrhsMinBlocks<typename LinksT::T, RB>::value) wilson_mrhs_kernel(Geom g, int V, LinksT U, FieldT in, int nrhs, Epi epi) {
   using T = typename LinksT::T;
-  const int r0 = blockIdx.y * RB;
-  unsigned active = 0;
-#pragma unroll
-  for (int j = 0; j < RB; ++j)
-    if (r0 + j < nrhs && epi.running(r0 + j)) active |= 1u << j;
   using A = typename Accum<T>::type;
-  A part[RB];
-#pragma unroll
-  for (int j = 0; j < RB; ++j) part[j] = A(0);
-  if (active) {
+  __shared__ A spart[Epi::kReduce ? kMaxRhs : 1][kBlock];
+  unsigned run = 0;
+  for (int q = 0; q < nrhs; ++q)
+    if (epi.running(q)) run |= 1u << q;
+  if constexpr (Epi::kReduce)
+    for (int q = 0; q < nrhs; ++q) spart[q][threadIdx.x] = A(0);
+  if (run) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
       int c[4];
       full_site(g, i, c);
-      spinor<T> acc[RB];
+#pragma unroll 1
+      for (int r0 = 0; r0 < nrhs; r0 += RB) {
+        const unsigned active = (run >> r0) & ((1u << RB) - 1u);
+        if (!active) continue;
+        // an opaque copy of the links pointer keeps the link loads inside this loop (hoisting all
+        // eight links out of it would hold 144 registers)
+        LinksT Ur = U;
+        asm volatile("" : "+l"(Ur.p));
+        spinor<T> acc[RB];
 #pragma unroll
-      for (int j = 0; j < RB; ++j) zero(acc[j]);
+        for (int j = 0; j < RB; ++j) zero(acc[j]);
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu)
+        for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
-        for (int dir = 0; dir < 2; ++dir) {
-          const int nb = w_neighbour(g, i, c, mu, dir);
-          const su3<T> Ul = U.load(mu, dir == 0 ? i : nb);
+          for (int dir = 0; dir < 2; ++dir) {
+            const int nb = w_neighbour(g, i, c, mu, dir);
+            const su3<T> Ul = Ur.load(mu, dir == 0 ? i : nb);
 #pragma unroll
-          for (int j = 0; j < RB; ++j)
-            if ((active >> j) & 1u) hop_accumulate<G5IN>(acc[j], Ul, in.at(r0 + j).load(nb), mu, dir);
-        }
+            for (int j = 0; j < RB; ++j)
+              if ((active >> j) & 1u) hop_accumulate<G5IN>(acc[j], Ul, in.at(r0 + j).load(nb), mu, dir);
+          }
 #pragma unroll
-      for (int j = 0; j < RB; ++j)
-        if ((active >> j) & 1u) epi.site(i, r0 + j, acc[j], part[j]);
+        for (int j = 0; j < RB; ++j)
+          if ((active >> j) & 1u) {
+            A part = A(0);
+            epi.site(i, r0 + j, acc[j], part);
+            if constexpr (Epi::kReduce) spart[r0 + j][threadIdx.x] += part;
+          }
+      }
     }
   }
   if constexpr (Epi::kReduce) {
-    double red[RB];
-#pragma unroll
-    for (int j = 0; j < RB; ++j) red[j] = (double)part[j];
-    if (mrhs_arrive<RB>(red, r0, nrhs, epi.partials, epi.counter())) {
+    __shared__ bool am_last;
+    for (int q = 0; q < nrhs; ++q) {
+      double v[1] = {(double)spart[q][threadIdx.x]};
+      block_sum<1>(v);
+      if (threadIdx.x == 0) epi.partials[(size_t)q * kMaxPartials + blockIdx.x] = v[0];
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      am_last = atomicAdd(epi.counter(), 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (am_last) {
       __shared__ double tot[kMaxRhs];
       mrhs_totals(nrhs, epi.partials, tot);
       if (threadIdx.x == 0) {
@@ -782,13 +814,13 @@ static dim3 w_grid(KernelT kernel, long long V, int gy) {
   return dim3((unsigned)(gx > 0 ? gx : 1), (unsigned)gy);
 }
 
-// register block of right-hand sides: the opts value if given (1, 2, 4 in FP32; 1, 2 in FP64), else
-// 2 in FP32 (128 registers, two blocks per SM; 4 needs about 250) and 1 in FP64 (2 spills)
+// register block of right-hand sides: the opts value if given (1, 2, 4 in FP32; 1, 2 in FP64), else 1
+// (measured fastest for 8 RHS on 32^3x64 in FP32: 177 ms of operator time per solve against 207 ms
+// for 2 and 265 ms for 4)
 int wilson_rhs_block(int prec, int R, int requested) {
   const int cap = prec == QCD_PREC_DOUBLE ? 2 : 4;
   if (requested > 0) return (requested == 1 || requested == 2 || requested == 4) && requested <= cap ? requested : -1;
-  const int def = prec == QCD_PREC_DOUBLE ? 1 : 2;
-  return R < def ? R : def;
+  return 1;
 }
 
 template <int PREC, int RB>
@@ -799,16 +831,15 @@ static int wilson_op_mrhs_typed(const qcd_lattice* lat, void* out, const void* i
   const int V = (int)lat->V;
   auto U = wl<PREC>(lat->wilson_links[PREC], V);
   const FT fin = wf<PREC>(const_cast<void*>(in), V), fout = wf<PREC>(out, V);
-  const int gy = (R + RB - 1) / RB;
   if (mode == 0) {
     auto k = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RB, WOpM<FT, 0>>;
-    k<<<w_grid(k, V, gy), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 0>{fin, fout, kappa, nullptr});
+    k<<<w_grid(k, V, 1), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 0>{fin, fout, kappa, nullptr});
   } else if (mode == 1) {
     auto k = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RB, WOpM<FT, 1>>;
-    k<<<w_grid(k, V, gy), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 1>{fin, fout, kappa, nullptr});
+    k<<<w_grid(k, V, 1), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 1>{fin, fout, kappa, nullptr});
   } else {
     auto k = wilson_mrhs_kernel<WLinks<PREC>, FT, true, RB, WOpM<FT, 2>>;
-    k<<<w_grid(k, V, gy), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 2>{fin, fout, kappa, nullptr});
+    k<<<w_grid(k, V, 1), kBlock, 0, st>>>(g, V, U, fin, R, WOpM<FT, 2>{fin, fout, kappa, nullptr});
   }
   QCD_CUDA(cudaGetLastError());
   return QCD_OK;
@@ -816,12 +847,9 @@ static int wilson_op_mrhs_typed(const qcd_lattice* lat, void* out, const void* i
 
 int launch_wilson_op_mrhs(const qcd_lattice* lat, void* out, const void* in, int R, double kappa, int mode, int prec,
                           cudaStream_t st) {
-  // the default register blocks: 1 in FP64, 2 in FP32 (1 for a single RHS)
+  // the default register block (1)
   if (prec == QCD_PREC_DOUBLE) return wilson_op_mrhs_typed<QCD_PREC_DOUBLE, 1>(lat, out, in, R, kappa, mode, st);
-  if (prec == QCD_PREC_SINGLE) {
-    if (wilson_rhs_block(prec, R, 0) == 1) return wilson_op_mrhs_typed<QCD_PREC_SINGLE, 1>(lat, out, in, R, kappa, mode, st);
-    return wilson_op_mrhs_typed<QCD_PREC_SINGLE, 2>(lat, out, in, R, kappa, mode, st);
-  }
+  if (prec == QCD_PREC_SINGLE) return wilson_op_mrhs_typed<QCD_PREC_SINGLE, 1>(lat, out, in, R, kappa, mode, st);
   return QCD_ERR_UNSUPPORTED;
 }
 
@@ -851,10 +879,9 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
   const F64 xh = wf<QCD_PREC_DOUBLE>(w.x_hi, V), t64 = wf<QCD_PREC_DOUBLE>(w.t64, V);
   const int grid = one_wave_grid(V, wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true, WEpiResidual<FT, false>>);
   const int grid_ru = one_wave_grid(V, wilson_kernel<WLinks<PREC>, FT, true, WEpiReliableInner<FT>>);
-  const int gy = (R + RB - 1) / RB;
   auto K1 = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RB, WEpiT<FT>>;
   auto K2 = wilson_mrhs_kernel<WLinks<PREC>, FT, true, RB, WEpiUpdate<FT, FT>>;
-  const dim3 gp = w_grid(w_p_kernel<FT>, V, R), g1 = w_grid(K1, V, gy), g2 = w_grid(K2, V, gy);
+  const dim3 gp = w_grid(w_p_kernel<FT>, V, R), g1 = w_grid(K1, V, 1), g2 = w_grid(K2, V, 1);
   const size_t cbytes = (size_t)V * 12 * sizeof(double2);  // one canonical spinor field
   long long launches = 0;
 
