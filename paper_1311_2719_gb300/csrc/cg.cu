@@ -69,7 +69,7 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
   R.w = carve(lat, PREC, 1, (char*)ws);
   R.st = st;
   R.tps = threads_per_site(PREC, lat->Vh);
-  R.grid = cg_grid<PREC, RECON>(lat->Vh, R.tps);
+  cg_launch_shape((long long)lat->Vh * R.tps, cg_grid<PREC, RECON>(lat->Vh, R.tps), &R.grid, &R.block);
   const bool mixed = PREC != QCD_PREC_DOUBLE;
 
   CgScalars h{};

@@ -25,7 +25,7 @@ __device__ __forceinline__ bool finite_pos(double v) { return isfinite(v) && v >
 
 // ---------------------------------------------------------------- init: r = b_e, x = 0, p = 0
 template <class FieldT, class XFieldT>
-__global__ void __launch_bounds__(kBlock) cg_init_kernel(Geom g, const double2* __restrict__ b_canon,
+__global__ void __launch_bounds__(kSpreadBlockMax) cg_init_kernel(Geom g, const double2* __restrict__ b_canon,
                                                          Field<QCD_PREC_DOUBLE> b_hi, Field<QCD_PREC_DOUBLE> x_hi,
                                                          FieldT r, FieldT p, XFieldT x_lo, int mixed, CgScalars* sc,
                                                          double* partials) {
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kBlock) cg_init_kernel(Geom g, const double2* 
 
 // ---------------------------------------------------------------- K3: p = r + beta p
 template <class FieldT>
-__global__ void __launch_bounds__(kBlock) cg_p_kernel(int Vh, FieldT r, FieldT p, CgScalars* sc, double* partials) {
+__global__ void __launch_bounds__(kSpreadBlockMax) cg_p_kernel(int Vh, FieldT r, FieldT p, CgScalars* sc, double* partials) {
   using T = typename FieldT::T;
   if (sc->done != kRunning) return;
   const T beta = (T)sc->beta;
@@ -200,7 +200,7 @@ __device__ __forceinline__ bool ru_wanted(const CgScalars* sc) {
 
 // x_hi += x_lo, x_lo = 0. With `gate`, the kernel returns at once unless ru_wanted(gate).
 template <class XFieldT>
-__global__ void __launch_bounds__(kBlock) ru_accumulate_kernel(int Vh, Field<QCD_PREC_DOUBLE> x_hi, XFieldT x_lo,
+__global__ void __launch_bounds__(kSpreadBlockMax) ru_accumulate_kernel(int Vh, Field<QCD_PREC_DOUBLE> x_hi, XFieldT x_lo,
                                                                const CgScalars* gate = nullptr) {
   using TX = typename XFieldT::T;
   if (gate && !ru_wanted(gate)) return;
@@ -311,7 +311,7 @@ struct EpiResidual {
 };
 
 // Write x (even sites) and y (odd sites) into canonical fields, zeroing the other halves.
-static __global__ void __launch_bounds__(kBlock) cg_output_kernel(Geom g, double2* __restrict__ x_canon,
+static __global__ void __launch_bounds__(kSpreadBlockMax) cg_output_kernel(Geom g, double2* __restrict__ x_canon,
                                                            double2* __restrict__ y_canon, Field<QCD_PREC_DOUBLE> x_e,
                                                            Field<QCD_PREC_DOUBLE> y_o) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.Vh; k += gridDim.x * blockDim.x) {
@@ -402,14 +402,15 @@ struct CgRunner {
   CgWork w;
   cudaStream_t st;
   int grid;
-  int tps = 1;  // threads per site of the operator kernels
+  int block = kBlock;  // threads per block of every kernel of the runner (<= kBlock)
+  int tps = 1;         // threads per site of the operator kernels
   long long launches = 0;
 
   // One operator launch with epilogue `epi` at the runner's threads-per-site.
   template <class LinksT, class InT, class Epi>
   void op(const LinksT& U, const InT& in, int out_par, const Epi& epi) {
-    if (tps == 2) dslash_kernel<LinksT, InT, Epi, 2><<<grid, kBlock, 0, st>>>(g, U, in, out_par, epi);
-    else dslash_kernel<LinksT, InT, Epi, 1><<<grid, kBlock, 0, st>>>(g, U, in, out_par, epi);
+    if (tps == 2) dslash_kernel<LinksT, InT, Epi, 2><<<grid, block, 0, st>>>(g, U, in, out_par, epi);
+    else dslash_kernel<LinksT, InT, Epi, 1><<<grid, block, 0, st>>>(g, U, in, out_par, epi);
   }
 
   // One CG iteration (K3, K1, K2). With `ev` (4 events) the two operator launches are bracketed.
@@ -417,7 +418,7 @@ struct CgRunner {
     auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
     FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh), ap = make_field<PREC>(w.ap, g.Vh);
     XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
-    cg_p_kernel<<<grid, kBlock, 0, st>>>(g.Vh, r, p, w.sc, w.partials);
+    cg_p_kernel<<<grid, block, 0, st>>>(g.Vh, r, p, w.sc, w.partials);
     if (ev) QCD_CUDA(cudaEventRecord(ev[0], st));
     op(U, p, QCD_ODD, EpiAp<FieldT>{ap, w.sc, w.partials});
     if (ev) QCD_CUDA(cudaEventRecord(ev[1], st));
@@ -433,7 +434,7 @@ struct CgRunner {
     FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh);
     XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
     launches += 1;
-    cg_init_kernel<<<grid, kBlock, 0, st>>>(g, (const double2*)b_canon, make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh),
+    cg_init_kernel<<<grid, block, 0, st>>>(g, (const double2*)b_canon, make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh),
                                             make_field<QCD_PREC_DOUBLE>(w.x_hi, g.Vh), r, p, x,
                                             PREC != QCD_PREC_DOUBLE, w.sc, w.partials);
     QCD_CUDA(cudaGetLastError());
@@ -450,7 +451,7 @@ struct CgRunner {
     auto tmp = make_field<QCD_PREC_DOUBLE>(w.tmp_o, g.Vh);
     launches += PREC != QCD_PREC_DOUBLE ? 3 : 2;
     if (PREC != QCD_PREC_DOUBLE)  // plain FP64: x_lo is x_hi itself
-      ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh),
+      ru_accumulate_kernel<<<grid, block, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh),
                                                     gated ? w.sc : nullptr);
     EpiStore<Field<QCD_PREC_DOUBLE>> store{tmp};
     EpiReliable<FieldT> rel{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, make_field<PREC>(w.r, g.Vh), w.sc,
@@ -472,10 +473,10 @@ struct CgRunner {
     auto tmp = make_field<QCD_PREC_DOUBLE>(w.tmp_o, g.Vh);
     launches += PREC != QCD_PREC_DOUBLE ? 4 : 3;
     if (PREC != QCD_PREC_DOUBLE)
-      ru_accumulate_kernel<<<grid, kBlock, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh));
+      ru_accumulate_kernel<<<grid, block, 0, st>>>(g.Vh, xh, make_field<XPREC::value>(w.x_lo, g.Vh));
     op(U64, xh, QCD_ODD, EpiStore<Field<QCD_PREC_DOUBLE>>{tmp});
     op(U64, tmp, QCD_EVEN, EpiResidual{make_field<QCD_PREC_DOUBLE>(w.b_hi, g.Vh), xh, w.sc, w.partials});
-    cg_output_kernel<<<grid, kBlock, 0, st>>>(g, (double2*)x_canon, (double2*)y_canon, xh, tmp);
+    cg_output_kernel<<<grid, block, 0, st>>>(g, (double2*)x_canon, (double2*)y_canon, xh, tmp);
     QCD_CUDA(cudaGetLastError());
     return QCD_OK;
   }
@@ -489,6 +490,26 @@ inline int cg_grid(long long Vh, int tps) {
   using XFieldT = Field<x_prec(PREC)>;
   if (tps == 2) return one_wave_grid(Vh, dslash_kernel<Links<PREC, RECON>, FieldT, EpiUpdate<FieldT, XFieldT>, 2>, 2);
   return one_wave_grid(Vh, dslash_kernel<Links<PREC, RECON>, FieldT, EpiUpdate<FieldT, XFieldT>, 1>, 1);
+}
+
+// Launch shape of the single-RHS CG kernels: the one-wave grid of 128-thread blocks; when the
+// lattice needs less than one wave, one block per SM with the sites spread evenly (blocks of
+// ceil(threads / SMs), rounded up to whole warps). The busiest SM sets the time of the pipe-bound
+// operator: 16^4 = 32768 sites per parity in 128-thread blocks puts 256 sites on some SMs against
+// 216 on average; 147 blocks of 224 put at most 224 on one.
+inline void cg_launch_shape(long long threads, int wave_grid, int* grid, int* block) {
+  *grid = wave_grid;
+  *block = kBlock;
+  if ((threads + kBlock - 1) / kBlock > wave_grid) return;  // at least a full wave
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1)
+    return;
+  long long b = (threads + sms - 1) / sms;
+  b = (b + 31) / 32 * 32;
+  if (b <= kBlock || b > kSpreadBlockMax) return;
+  *block = (int)b;
+  *grid = (int)((threads + b - 1) / b);
 }
 
 inline int read_scalars(const CgWork& w, CgScalars* h, cudaStream_t st, int count = 1) {

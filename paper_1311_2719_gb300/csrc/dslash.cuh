@@ -110,8 +110,15 @@ struct MinBlocks {
       sizeof(typename LinksT::T) == 4 ? 8 : (std::is_same<typename LinksT::T, double>::value ? 5 : 4);
 };
 
+// The same budget as a register cap, so that a launch may also use wider blocks (one block per SM
+// on lattices smaller than a wave, see cg_launch_shape): 64 / 96 / 128 registers.
+template <class LinksT>
+struct MaxRegs {
+  static constexpr int value = 65536 / (kBlock * MinBlocks<LinksT>::value) / 8 * 8;
+};
+
 template <class LinksT, class FieldT, class Epi, int TPS = 1>
-__global__ void __launch_bounds__(kBlock, MinBlocks<LinksT>::value) dslash_kernel(Geom g, LinksT U, FieldT in,
+__global__ void __maxnreg__(MaxRegs<LinksT>::value) dslash_kernel(Geom g, LinksT U, FieldT in,
                                                                                  int out_par, Epi epi) {
   if (epi.skip()) return;
   using A = typename Accum<typename LinksT::T>::type;

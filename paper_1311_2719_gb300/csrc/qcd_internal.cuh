@@ -13,6 +13,7 @@
 namespace qcd {
 
 constexpr int kBlock = 128;           // threads per block of the site kernels
+constexpr int kSpreadBlockMax = 512;  // widest block of the CG kernels on lattices below one wave
 constexpr int kMaxPartials = 8192;    // per-reduction partial slots in the workspace
 constexpr int kMaxRhs = 16;
 
