@@ -69,6 +69,9 @@ WORKLOADS = {
                                inner="single18", nrhs=1,
                                desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion with "
                                     "FP64 reliable updates, to 1e-10"),
+    "force32_fp64": dict(kind_solve="force", dims=(32, 32, 32, 32), mass=0.1, tol=1e-10,
+                         desc="staggered fermion force on every link of a 32^4 Haar lattice from the CG's x and "
+                              "y = D_oe x (m = 0.1), FP64"),
     "batch64_single12": dict(kind_solve="batched", n=64, tol=1e-10, inner="single12",
                              desc="64 independent staggered lattices {4^4,6^4,8^4,8^3x16}, m in [0.02,0.5], one "
                                   "persistent clustered CG launch: FP32 recon-12 inner, FP64 reliable updates"),
@@ -140,7 +143,8 @@ def sources_sha(files) -> str:
 
 
 def ncu_traffic(workload):
-    """DRAM bytes per operator launch (mean of K1 and K2) from profiles/ncu_traffic.json, or None when
+    """DRAM bytes per launch of the workload's dominant kernel (the mean of K1 and K2 for a CG) from
+    profiles/ncu_traffic.json, or None when
     the file has no entry for the workload or the entry was taken on other kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
@@ -149,7 +153,7 @@ def ncu_traffic(workload):
             return None
     except (OSError, ValueError, KeyError):
         return None
-    return (w["K1_bytes"] + w["K2_bytes"]) / 2
+    return w["bytes"] if "bytes" in w else (w["K1_bytes"] + w["K2_bytes"]) / 2
 
 
 def _half_dslash_count(info):
@@ -707,6 +711,137 @@ def run_gpu_wilson(args, wl):
     return out if rank == 0 else None
 
 
+FORCE_FLOP_PER_LINK = 162  # U b (66) + a b^dagger (54) + coefficient (6) + i (W - W^dagger) (18) + trace removal (18)
+
+
+def run_gpu_force(args, wl):
+    """The fermion force on every link of the lattice from the CG's x and y = D_oe x (a mixed CG
+    solve produces them once, outside the timed region). One step = qcd_fermion_force on the whole
+    lattice; value = GFLOP/s at 162 flop per link; the kernel is bound by the FP64 pipe on GB300."""
+    import numpy as np
+    import torch
+
+    from paper_1311_2719_gb300 import inputs as I
+    from paper_1311_2719_gb300 import qcd as Q
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dims, mass = wl["dims"], wl["mass"]
+    stream = torch.cuda.Stream()
+    lat = Q.Lattice(dims)
+    V = lat.V
+    U_np = I.make_links(dims, kind="haar", seed=1)
+    U_host = torch.from_numpy(U_np).pin_memory()
+    U_dev = U_host.to("cuda")
+    b_dev = torch.from_numpy(I.make_source(dims, seed=2)).cuda()
+    x_dev, y_dev = torch.zeros_like(b_dev), torch.zeros_like(b_dev)
+    for p, r in ((0, 18), (1, 12)):
+        lat.load_links(U_dev, p, r)
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner, opts.recon_inner = 1, 12
+    ws = lat.workspace(opts)
+    with torch.cuda.stream(stream):
+        rc, info = Q.qcd_cg_solve(lat.handle, x_dev, b_dev, mass, 1e-10, 100000, opts, ws, y_dev, stream=stream)
+    if rc != Q.QCD_OK:
+        raise RuntimeError(f"CG for the force inputs failed: {Q.qcd_status_string(rc)}")
+    del ws
+    x_host = x_dev.cpu().pin_memory()
+    y_host = y_dev.cpu().pin_memory()
+    f_dev = torch.empty((V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    f_host = torch.empty((V, 4, 3, 3), dtype=torch.complex128).pin_memory()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(host_io=False):
+        with torch.cuda.stream(stream):
+            if host_io:
+                U_dev.copy_(U_host, non_blocking=True)
+                x_dev.copy_(x_host, non_blocking=True)
+                y_dev.copy_(y_host, non_blocking=True)
+            Q.qcd_fermion_force(lat.handle, f_dev, U_dev, x_dev, y_dev, stream)
+            if host_io:
+                f_host.copy_(f_dev, non_blocking=True)
+
+    def timed(n, host_io=False):
+        ms = []
+        for _ in range(n):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(host_io)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    proc, cpath = _clock_sampler(uuid)
+    time.sleep(0.3)
+    ms = timed(args.steps)
+    clocks = _clock_summary(proc, cpath)
+    ms_e2e = timed(args.steps, host_io=True)
+    flops = FORCE_FLOP_PER_LINK * 4 * V
+    tot = torch.tensor([sum(ms), sum(ms_e2e)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    t_ms, t_e2e = tot.tolist()
+    value = world * args.steps * flops / (t_ms * 1e-3) / 1e9
+    per = t_ms / args.steps
+    achieved = flops / (per * 1e-3) / 1e12
+    alg_bytes = 1200 * V  # links 576 + force 576 + the site's own x or y 48 B per site
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(per, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Haar SU(3) links, Gaussian source; x, y from the CG)",
+        "config": {"workload": wl["desc"], "dims": list(dims), "mass": mass, "parallelism": f"replicas x{world} (no sharding)",
+                   "l2": "flushed before every step (512 MB write, outside the timed events)",
+                   "step": "qcd_fermion_force (every link)"},
+        "roofline": {"bound": "alu", "kernel": "force_kernel", "achieved": round(achieved, 4),
+                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                     "peak_source": "derived FP64 FMA peak (152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz)",
+                     "traffic": ncu_traffic(args.workload), "alg_bytes_per_launch": alg_bytes,
+                     "hbm_model_gbs": round(alg_bytes / (per * 1e-3) / 1e9, 1),
+                     "hbm_model_frac": round(alg_bytes / (per * 1e-3) / 1e9 / hbm_peak, 4),
+                     "alg_flops_per_launch": flops, "avg_launch_us": round(per * 1e3, 3)},
+        "e2e": {"value": round(world * args.steps * flops / (t_e2e * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int((U_host.numel() + x_host.numel() + y_host.numel()) * 16),
+                "d2h_bytes_per_step": int(f_host.numel() * 16), "ms_per_step": round(t_e2e / args.steps, 4)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "cg_for_inputs": {"iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import force as Fo
+        t0 = time.perf_counter()
+        Fo.fermion_force(U_np, x_host.numpy(), y_host.numpy(), dims)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": round(flops / dt / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                               "sample": f"FP64 numpy oracle: the force on every link of the {dims} lattice ({dt:.1f} s), "
+                                         f"{FORCE_FLOP_PER_LINK} flop/link"}
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
 def _wilson_oracle_sample(wl, U=None, b=None):
     """One application of M = 1 - kappa D_W by the FP64 oracle on the full lattice (flops, seconds)."""
     from oracle import wilson as Wo
@@ -776,6 +911,24 @@ def run_reference(args, wl):
         what = (f"each step: FP64 numpy oracle Wilson D_W at every 32nd site ({len(sites)} sites) of the {dims} "
                 f"lattice, 1320 flop/site, 1 thread")
         cfg = {"dims": list(dims), "kappa": wl["kappa"], "nrhs": wl["nrhs"]}
+    elif kind == "force":
+        from oracle import force as Fo
+        dims = wl["dims"]
+        U = I.make_links(dims, kind="haar", seed=1)
+        x, y = I.make_source(dims, seed=2), I.make_source(dims, seed=3)
+        V = U.shape[0]
+        sites = np.arange(0, V, 64)
+        sites4 = np.repeat(sites, 4)
+        mus4 = np.tile(np.arange(4), len(sites))
+
+        def sample():
+            t0 = time.perf_counter()
+            Fo.fermion_force_links(U, x, y, dims, sites4, mus4)
+            return FORCE_FLOP_PER_LINK * len(sites4), time.perf_counter() - t0
+
+        what = (f"each step: FP64 numpy oracle force on the links of every 64th site ({len(sites)} sites) of the "
+                f"{dims} lattice, {FORCE_FLOP_PER_LINK} flop/link, 1 thread")
+        cfg = {"dims": list(dims), "mass": wl["mass"]}
     else:
         if kind == "batched":  # the largest lattice of the batch stands in for the batch
             spec = max(I.make_lattice_batch(wl["n"], seed=4), key=lambda t: int(np.prod(t[0])))
@@ -834,6 +987,8 @@ def main():
         out = run_gpu_batched(args, wl)
     elif wl.get("kind_solve") == "wilson":
         out = run_gpu_wilson(args, wl)
+    elif wl.get("kind_solve") == "force":
+        out = run_gpu_force(args, wl)
     else:
         out = run_gpu(args, wl)
     if out is not None:

@@ -248,6 +248,22 @@ QCD_API size_t qcd_workspace_bytes_full(const qcd_lattice* lat, const qcd_solver
 QCD_API int qcd_solve_full(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass, double tol, int max_iter,
                    const qcd_solver_opts* opts, void* workspace_dev, qcd_solve_info* info, void* stream);
 
+/* ---- fermion force (for the paper's molecular-dynamics program, §2, fed by the CG of §4) ------ */
+
+/* The force of the even-site pseudofermion action S = phi_e^dagger (m^2 - D_eo D_oe)^-1 phi_e on
+ * every link, from the two fields qcd_cg_solve returns: x = A^-1 phi_e (even sites) and
+ * y = D_oe x (odd sites). force_dev[n][mu] is the traceless Hermitian 3x3 matrix G_mu(n) with
+ * dS = eps tr(H G_mu(n)) when U_mu(n) -> exp(i eps H) U_mu(n) (H traceless Hermitian); with
+ * c = eta_mu(n) zeta_mu(n) / 2 (zeta = the handle's tbc on the last time slice's t-links),
+ *   n even: W = c (U_mu(n) y(n+mu)) x(n)^dagger;   n odd: W = c y(n) (U_mu(n) x(n+mu))^dagger;
+ *   G_mu(n) = i (W - W^dagger) - tr(i (W - W^dagger)) / 3.
+ *   links_dev : device, canonical complex128[V][4][3][3] (the field given to qcd_load_links).
+ *   x_dev, y_dev : device, complex128[V][3]; only the even half of x and the odd half of y are read.
+ *   force_dev : device, complex128[V][4][3][3], overwritten; must not alias the inputs.
+ * FP64 throughout; asynchronous on `stream`. */
+QCD_API int qcd_fermion_force(const qcd_lattice* lat, void* force_dev, const void* links_dev, const void* x_dev,
+                      const void* y_dev, void* stream);
+
 /* ---- Wilson fermions (the paper's second program, §2 and §6) --------------------------------- */
 
 /* Wilson hopping term on the full lattice (no even-odd reduction), DeGrand-Rossi gamma matrices

@@ -46,6 +46,7 @@ int launch_wilson_op(const qcd_lattice*, void*, const void*, double, int, int, c
 int run_wilson_cgnr(qcd_lattice*, int, void*, const void*, double, double, int, const qcd_solver_opts&, void*,
                     qcd_solve_info*, cudaStream_t);
 size_t full_workspace_bytes(const qcd_lattice*, int);
+int launch_fermion_force(const qcd_lattice*, void*, const void*, const void*, const void*, cudaStream_t);
 int run_solve_full(qcd_lattice*, void*, const void*, double, double, int, const qcd_solver_opts&, void*,
                    qcd_solve_info*, cudaStream_t);
 int run_cg_batched(int, qcd_lattice* const*, void* const*, const void* const*, void* const*, const double*, double, int,
@@ -406,6 +407,18 @@ int qcd_solve_full(qcd_lattice* lat, void* x_dev, const void* b_dev, double mass
   qcd_solver_opts o;
   if (int rc = check_solve_args(lat, x_dev, b_dev, workspace_dev, nullptr, mass, tol, max_iter, opts, o)) return done(rc);
   return done(run_solve_full(lat, x_dev, b_dev, mass, tol, max_iter, o, workspace_dev, info, as_stream(stream)));
+}
+
+int qcd_fermion_force(const qcd_lattice* lat, void* force_dev, const void* links_dev, const void* x_dev,
+                      const void* y_dev, void* stream) {
+  if (!lat) return invalid("lat is NULL");
+  if (int rc = check_dev_ptr(force_dev, "force_dev")) return rc;
+  if (int rc = check_dev_ptr(links_dev, "links_dev")) return rc;
+  if (int rc = check_dev_ptr(x_dev, "x_dev")) return rc;
+  if (int rc = check_dev_ptr(y_dev, "y_dev")) return rc;
+  if (force_dev == links_dev || force_dev == x_dev || force_dev == y_dev)
+    return invalid("force_dev must not alias links_dev, x_dev or y_dev");
+  return launch_fermion_force(lat, force_dev, links_dev, x_dev, y_dev, as_stream(stream));
 }
 
 static bool wilson_prec(int p) { return p == QCD_PREC_DOUBLE || p == QCD_PREC_SINGLE; }

@@ -104,6 +104,7 @@ SIGNATURES = {
     "qcd_workspace_bytes_full": (_sz, [_vp, ctypes.POINTER(qcd_solver_opts)]),
     "qcd_solve_full": (_i, [_vp, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp,
                             ctypes.POINTER(qcd_solve_info), _vp]),
+    "qcd_fermion_force": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "qcd_wilson_field_bytes": (_sz, [_vp, _i]),
     "qcd_wilson_links_bytes": (_sz, [_vp, _i]),
     "qcd_wilson_load_links": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -309,6 +310,12 @@ def qcd_solve_full(lat, x_dev, b_dev, mass, tol, max_iter, opts, workspace_dev, 
     if rc in raise_on:
         _check(rc, "qcd_solve_full")
     return rc, info.as_dict()
+
+
+def qcd_fermion_force(lat, force_dev, links_dev, x_dev, y_dev, stream=None):
+    """force[n][mu] = G_mu(n), the traceless Hermitian derivative of phi^dagger A^-1 phi (x even, y odd)."""
+    return _check(_lib.qcd_fermion_force(lat, _ptr(force_dev), _ptr(links_dev), _ptr(x_dev), _ptr(y_dev),
+                                         _stream(stream)), "qcd_fermion_force")
 
 
 QCD_WILSON_DSLASH, QCD_WILSON_M, QCD_WILSON_MDAG = 0, 1, 2
