@@ -87,6 +87,14 @@ typedef struct {
                             at a time), 1/2/4/8/16; 0 = tuned value or 4                        */
   int block_size;        /* batched solves: threads per block, multiple of 32 <= 256; 0 = tuned
                             value or 256                                                        */
+  int staged;            /* 1: the FP32 recon-12 operator of the single-RHS CG stages each tile's
+                            links and neighbour vectors in shared memory by bulk asynchronous
+                            copies (measured 2.4x slower on GB300: ~600 staged bytes per site
+                            leave 4 warps per SM); 0 (default): every thread loads its own
+                            operands                                                           */
+  long long wait_cycles; /* limit of a device-side wait on an mbarrier, in SM clock cycles (the
+                            staged operator); 0 = 4e9 (about 2 s). On expiry the solve returns
+                            QCD_ERR_TIMEOUT.                                                    */
 } qcd_solver_opts;
 
 /* What a solve reports. */

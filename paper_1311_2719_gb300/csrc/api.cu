@@ -170,6 +170,8 @@ void qcd_solver_opts_default(qcd_solver_opts* o) {
   o->rhs_block = 0;
   o->cluster_size = 0;
   o->block_size = 0;
+  o->staged = 0;
+  o->wait_cycles = 0;
 }
 
 size_t qcd_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts, int nrhs) {

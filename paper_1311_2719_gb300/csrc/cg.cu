@@ -70,6 +70,8 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
   R.st = st;
   R.tps = threads_per_site(PREC, lat->Vh);
   cg_launch_shape((long long)lat->Vh * R.tps, cg_grid<PREC, RECON>(lat->Vh, R.tps), &R.grid, &R.block);
+  R.setup_staged(o.staged != 0);
+  R.wait_cycles = o.wait_cycles > 0 ? o.wait_cycles : kWaitCycles;
   const bool mixed = PREC != QCD_PREC_DOUBLE;
 
   CgScalars h{};
@@ -120,6 +122,7 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
     if ((rc = read_scalars(R.w, &h, st))) { cleanup(); return rc; }
   }
   while (!use_graph) {
+    if (h.fault) break;  // reported below as QCD_ERR_TIMEOUT
     if (h.done == kBreakdown) { status = QCD_ERR_BREAKDOWN; break; }
     if (h.done == kMaxIter) { status = QCD_ERR_NOT_CONVERGED; break; }
     if (h.done == kTrueConverged) break;
@@ -152,7 +155,10 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
   if ((rc = R.finish(x, y))) return rc;
   if ((rc = read_scalars(R.w, &h, st))) return rc;
   const double true_rel = h.bb > 0 ? std::sqrt(h.res2 / h.bb) : 0.0;
-  if (status == QCD_OK && !(true_rel <= tol)) {
+  if (h.fault) {
+    set_error("a bounded device-side wait in the staged operator gave up");
+    status = QCD_ERR_TIMEOUT;
+  } else if (status == QCD_OK && !(true_rel <= tol)) {
     // The recursion met the tolerance but the FP64 residual did not (possible in plain FP64 CG
     // for very small tol); report it rather than claim convergence.
     status = QCD_ERR_NOT_CONVERGED;

@@ -6,6 +6,7 @@
 #include <type_traits>
 
 #include "dslash.cuh"
+#include "dslash_staged.cuh"
 
 
 namespace qcd {
@@ -13,6 +14,7 @@ namespace qcd {
 struct __align__(256) CgScalars {
   double rr, rr_prev, pp, alpha, beta, delit, bb, m2, res2, rmax2, delta2, tol2;
   int iter, max_iter, done, since_ru, ru_count, ru_interval, mixed, loops;
+  int fault;  // set by a kernel whose bounded device-side wait gave up
   unsigned counter[16];
 };
 static_assert(sizeof(CgScalars) <= 256, "scalars block");
@@ -282,7 +284,7 @@ struct Gated {
 // `max_loops` passes as a guard).
 static __global__ void cg_loop_control_kernel(CgScalars* sc, cudaGraphConditionalHandle handle, int max_loops) {
   const int loops = ++sc->loops;
-  cudaGraphSetConditional(handle, (sc->done == kRunning && loops < max_loops) ? 1u : 0u);
+  cudaGraphSetConditional(handle, (sc->done == kRunning && sc->fault == 0 && loops < max_loops) ? 1u : 0u);
 }
 
 // Final true residual: res = b - (m^2 x - D_eo y), y = D_oe x.
@@ -406,9 +408,50 @@ struct CgRunner {
   int tps = 1;         // threads per site of the operator kernels
   long long launches = 0;
 
+  int staged_grid = 0;  // > 0: FP32 recon-12 operator launches use the staged kernel with this grid
+  long long wait_cycles = kWaitCycles;
+
+  // Enable the staged operator (FP32 recon-12, 16-byte aligned links; it maps one thread to one site
+  // of a tile whatever `tps` says) and size its persistent grid: all resident blocks, at most one
+  // per tile.
+  void setup_staged(bool want) {
+    staged_grid = 0;
+    if constexpr (PREC == QCD_PREC_SINGLE && RECON == 12) {
+      const void* lp = lat->links[PREC].ptr;
+      if (!want || ((uintptr_t)lp & 15u) != 0) return;
+      const int smem = 2 * (int)sizeof(StageFp32R12);
+      auto k1 = dslash_staged_fp32r12_kernel<EpiAp<FieldT>>;
+      auto k2 = dslash_staged_fp32r12_kernel<EpiUpdate<FieldT, XFieldT>>;
+      if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+          cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+      }
+      int dev = 0, sms = 0, per1 = 0, per2 = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k1, kStageSites, smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, kStageSites, smem) != cudaSuccess || per1 < 1 || per2 < 1) {
+        cudaGetLastError();
+        return;
+      }
+      const long long tiles = (g.Vh + kStageSites - 1) / kStageSites;
+      long long gr = (long long)sms * (per1 < per2 ? per1 : per2);
+      if (gr > tiles) gr = tiles;
+      if (gr > kMaxPartials) gr = kMaxPartials;
+      staged_grid = (int)gr;
+    }
+  }
+
   // One operator launch with epilogue `epi` at the runner's threads-per-site.
   template <class LinksT, class InT, class Epi>
   void op(const LinksT& U, const InT& in, int out_par, const Epi& epi) {
+    if constexpr (std::is_same<LinksT, Links<QCD_PREC_SINGLE, 12>>::value && std::is_same<InT, Field<QCD_PREC_SINGLE>>::value) {
+      if (staged_grid > 0) {
+        dslash_staged_fp32r12_kernel<Epi><<<staged_grid, kStageSites, 2 * sizeof(StageFp32R12), st>>>(
+            g, U, in, out_par, epi, &w.sc->fault, wait_cycles);
+        return;
+      }
+    }
     if (tps == 2) dslash_kernel<LinksT, InT, Epi, 2><<<grid, block, 0, st>>>(g, U, in, out_par, epi);
     else dslash_kernel<LinksT, InT, Epi, 1><<<grid, block, 0, st>>>(g, U, in, out_par, epi);
   }

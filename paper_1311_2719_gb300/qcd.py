@@ -49,6 +49,8 @@ class qcd_solver_opts(ctypes.Structure):
         ("rhs_block", ctypes.c_int),
         ("cluster_size", ctypes.c_int),
         ("block_size", ctypes.c_int),
+        ("staged", ctypes.c_int),
+        ("wait_cycles", ctypes.c_longlong),
     ]
 
 

@@ -83,10 +83,11 @@ class Rig:
         return np.stack(outs)
 
     def cg(self, b, mass, tol=1e-10, max_iter=10000, inner="double", use_graph=1, check_interval=8,
-           stream=None, want_y=True):
+           stream=None, want_y=True, staged=0):
         opts = Q.qcd_solver_opts_default()
         opts.prec_inner, opts.recon_inner = PRECS[inner]
         opts.use_graph = use_graph
+        opts.staged = staged
         opts.check_interval = check_interval
         ws = self.lat.workspace(opts)
         bd = dev(b)

@@ -190,3 +190,54 @@ def test_full_system_solve_16_4(H):
         assert rc == Q.QCD_OK and info["true_rel_residual"] <= 1e-10
         res = b - S.apply_m(U, x, dims, m)
         assert np.linalg.norm(res) / np.linalg.norm(b) <= 1.01e-10
+
+
+@pytest.mark.parametrize("dims,m", [((8, 8, 8, 8), 0.1), ((2, 4, 6, 8), 0.1), ((10, 4, 6, 8), 0.05), ((6, 6, 6, 6), 0.02),
+                                    ((16, 16, 16, 16), 0.1)])
+def test_staged_operator_cg_matches_oracle_and_direct(H, dims, m):
+    """The FP32 recon-12 CG with the operator's inputs staged in shared memory by bulk copies: same
+    solution as the oracle, graph == eager, and the same recursion as the direct-load kernel up to
+    rounding (ragged last tiles, runs clamped at both ends of the index range, wrapped neighbours)."""
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    rig = H.Rig(dims, U, precs=["double", "single12"])
+    rc, info, x, y = rig.cg(b, m, inner="single12", staged=1)
+    assert rc == Q.QCD_OK, info
+    assert info["true_rel_residual"] <= 1e-10
+    assert S.true_residual(U, x, b, dims, m) <= 1.01e-10
+    ref = S.cg_solve(U, b, dims, m, tol=1e-12, max_iter=20000)
+    assert H.rel(x, ref["x"]) <= _kappa_bound(m) * 1e-10
+    rc_e, info_e, x_e, _ = rig.cg(b, m, inner="single12", staged=1, use_graph=0)
+    assert rc_e == Q.QCD_OK and info_e["iterations"] == info["iterations"] and np.array_equal(x, x_e)
+    rc_d, info_d, x_d, _ = rig.cg(b, m, inner="single12", staged=0)
+    assert rc_d == Q.QCD_OK and abs(info_d["iterations"] - info["iterations"]) <= 2
+    assert H.rel(x, x_d) <= _kappa_bound(m) * 2e-10
+
+
+def test_staged_operator_wait_limit_reports_timeout(H):
+    """Failure detection without a GPU fault: a wait limit of one clock cycle makes the staged
+    operator's first wait on its bulk copies give up; the kernel records the fault, lets its copies
+    land, and the solve returns QCD_ERR_TIMEOUT. A default solve on the same buffers then succeeds."""
+    import torch
+    dims, m = (8, 8, 8, 8), 0.1
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    rig = H.Rig(dims, U, precs=["double", "single12"])
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner, opts.recon_inner = PRECS_SINGLE12
+    opts.staged, opts.wait_cycles = 1, 1
+    ws = rig.lat.workspace(opts)
+    bd = H.dev(b)
+    x, y = torch.zeros_like(bd), torch.zeros_like(bd)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    rc, info = Q.qcd_cg_solve(rig.h, x, bd, m, 1e-10, 1000, opts, ws, y, stream=s, raise_on=())
+    s.synchronize()
+    assert rc == Q.QCD_ERR_TIMEOUT and info["status"] == Q.QCD_ERR_TIMEOUT
+    opts.wait_cycles = 0
+    rc, info = Q.qcd_cg_solve(rig.h, x, bd, m, 1e-10, 1000, opts, ws, y, stream=s, raise_on=())
+    s.synchronize()
+    assert rc == Q.QCD_OK and info["true_rel_residual"] <= 1e-10
+
+
+PRECS_SINGLE12 = (Q.QCD_PREC_SINGLE, 12)
