@@ -156,6 +156,20 @@ def ncu_traffic(workload):
     return w["bytes"] if "bytes" in w else (w["K1_bytes"] + w["K2_bytes"]) / 2
 
 
+def reduce_over_ranks(max_vals, sum_vals, device="cuda"):
+    """Whole-job figures of N replicas: the elementwise max over ranks of `max_vals` (times) and the
+    sum of `sum_vals` (work done). With one process (no process group) the inputs come back as they
+    are. The caller's process group sets the backend (NCCL on GPUs; the tests use gloo on CPU)."""
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([float(v) for v in max_vals], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(v) for v in sum_vals], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.tolist(), sm.tolist()
+
+
 def _half_dslash_count(info):
     return 2 * info["iterations"] + 2 + 2 * info["reliable_updates"]
 
@@ -260,13 +274,8 @@ def run_gpu(args, wl):
     total_ms = sum(ms)
     total_ms_e2e = sum(ms_e2e)
     flops_e2e = [FLOP_PER_SITE * Vh * _half_dslash_count(i) for i in infos_e2e]
-    tot = torch.tensor([total_ms, total_ms_e2e], dtype=torch.float64, device="cuda")
-    fl = torch.tensor([sum(flops), sum(flops_e2e)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        dist.all_reduce(fl, op=dist.ReduceOp.SUM)
-    total_ms, total_ms_e2e = tot.tolist()
-    sum_flops, sum_flops_e2e = fl.tolist()
+    (total_ms, total_ms_e2e), (sum_flops, sum_flops_e2e) = reduce_over_ranks([total_ms, total_ms_e2e],
+                                                                             [sum(flops), sum(flops_e2e)])
     value = sum_flops / (total_ms * 1e-3) / 1e9
     e2e_value = sum_flops_e2e / (total_ms_e2e * 1e-3) / 1e9
 
@@ -481,12 +490,8 @@ def run_gpu_batched(args, wl):
     fp64_step()
     ms64, _ = timed(fp64_step, max(1, min(args.steps, 3)))
 
-    tot = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
-    fl = torch.tensor([float(sum(o[0] for o in outs))], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        dist.all_reduce(fl, op=dist.ReduceOp.SUM)
-    value = fl.item() / (tot.item() * 1e-3) / 1e9
+    (t_all,), (fl_all,) = reduce_over_ranks([sum(ms)], [sum(o[0] for o in outs)])
+    value = fl_all / (t_all * 1e-3) / 1e9
     infos = outs[-1][1]
     t_batched = sum(ms) / args.steps
     t_fp64 = sum(ms64) / len(ms64)
@@ -508,6 +513,47 @@ def run_gpu_batched(args, wl):
         "gpu_launches": int(sum(o[2] for o in outs)),
         "clocks": clocks,
     }
+    # roofline. Algorithmic bytes per output site of a half-lattice operator at the inner precision:
+    # links once per launch (shared by every RHS), and per RHS K1 = p in + ap out, K2 = ap in, p in,
+    # r and x read and written (x at FP32).
+    link_b, fld_b, x_b = {"single18": (576, 24, 24), "single12": (384, 24, 24), "half12": (192, 16, 24)}[inner]
+    k1_rhs = 2 * fld_b
+    k2_rhs = fld_b + fld_b + 2 * fld_b + 2 * x_b
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if wl["kind_solve"] == "mrhs":
+        opts.profile = 1
+        _, outs_p = timed(step, 1)
+        infos_p = outs_p[0][1]
+        opts.profile = 0
+        Vh = lats[0].Vh
+        d_ms, d_n = infos_p[0]["dslash_ms"], infos_p[0]["dslash_launches"]
+        pairs = max(i["iterations"] for i in infos_p)
+        rhs_its = sum(i["iterations"] for i in infos_p)
+        alg = Vh * (2 * link_b * pairs + (k1_rhs + k2_rhs) * rhs_its)
+        ach = alg / (d_ms * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": "dslash_mrhs_cg_kernel (K1+K2 launches)", "achieved": round(ach, 1),
+                           "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                           "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": ncu_traffic(args.workload),
+                           "alg_bytes_per_launch": round(alg / d_n), "avg_launch_us": round(d_ms / d_n * 1e3, 3),
+                           "alg_bytes_per_site": {"links_per_launch": link_b, "k1_per_rhs": k1_rhs, "k2_per_rhs": k2_rhs},
+                           "note": f"the links ({Q.qcd_links_bytes(lats[0].handle, prec_in, recon_in) / 1e6:.0f} MB) "
+                                   "stay in L2 across the RHS blocks"}
+    else:
+        # one persistent launch does every solve: algorithmic bytes of all its operator applications
+        # (2 per iteration per lattice) over the whole kernel time; the lattices (4^4..8^3x16) live in L2
+        alg = sum(l.Vh * (2 * link_b + k1_rhs + k2_rhs) * i["iterations"] for l, i in zip(lats, infos))
+        ach = alg / (t_batched * 1e-3) / 1e9
+        out["roofline"] = {"bound": "latency", "kernel": "batched_cg_kernel (whole batch, one launch)",
+                           "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                           "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": ncu_traffic(args.workload),
+                           "alg_bytes_per_launch": round(alg),
+                           "note": "L2-resident lattices; every CG step ends in a cluster barrier: latency-bound by design"}
     if world > 1:
         dist.destroy_process_group()
     return out if rank == 0 else None
@@ -638,14 +684,10 @@ def run_gpu_wilson(args, wl):
     t_op32 = op_time(1, 1)
     t_op32_r = op_time(1, R) if R > 1 else t_op32
 
-    tot = torch.tensor([sum(ms), sum(ms_e2e)], dtype=torch.float64, device="cuda")
-    fl = torch.tensor([float(flops_of(runs)), float(flops_of(runs_e2e))], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        dist.all_reduce(fl, op=dist.ReduceOp.SUM)
-    total_ms, total_ms_e2e = tot.tolist()
-    value = fl[0].item() / (total_ms * 1e-3) / 1e9
-    e2e_value = fl[1].item() / (total_ms_e2e * 1e-3) / 1e9
+    (total_ms, total_ms_e2e), (fl0, fl1) = reduce_over_ranks([sum(ms), sum(ms_e2e)],
+                                                              [flops_of(runs), flops_of(runs_e2e)])
+    value = fl0 / (total_ms * 1e-3) / 1e9
+    e2e_value = fl1 / (total_ms_e2e * 1e-3) / 1e9
     t_mixed, t_64 = sum(ms) / len(ms), sum(ms64) / len(ms64)
 
     # roofline of the FP32 operator launches inside the solve (K1: t = M p, K2: M^dagger t + update).
@@ -793,11 +835,8 @@ def run_gpu_force(args, wl):
     clocks = _clock_summary(proc, cpath)
     ms_e2e = timed(args.steps, host_io=True)
     flops = FORCE_FLOP_PER_LINK * 4 * V
-    tot = torch.tensor([sum(ms), sum(ms_e2e)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    t_ms, t_e2e = tot.tolist()
-    value = world * args.steps * flops / (t_ms * 1e-3) / 1e9
+    (t_ms, t_e2e), (fl_all,) = reduce_over_ranks([sum(ms), sum(ms_e2e)], [args.steps * flops])
+    value = fl_all / (t_ms * 1e-3) / 1e9
     per = t_ms / args.steps
     achieved = flops / (per * 1e-3) / 1e12
     alg_bytes = 1200 * V  # links 576 + force 576 + the site's own x or y 48 B per site
@@ -822,7 +861,7 @@ def run_gpu_force(args, wl):
                      "hbm_model_gbs": round(alg_bytes / (per * 1e-3) / 1e9, 1),
                      "hbm_model_frac": round(alg_bytes / (per * 1e-3) / 1e9 / hbm_peak, 4),
                      "alg_flops_per_launch": flops, "avg_launch_us": round(per * 1e3, 3)},
-        "e2e": {"value": round(world * args.steps * flops / (t_e2e * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+        "e2e": {"value": round(fl_all / (t_e2e * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int((U_host.numel() + x_host.numel() + y_host.numel()) * 16),
                 "d2h_bytes_per_step": int(f_host.numel() * 16), "ms_per_step": round(t_e2e / args.steps, 4)},
         "gpu_launches": args.steps,
