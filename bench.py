@@ -69,6 +69,9 @@ WORKLOADS = {
                                inner="single18", nrhs=1,
                                desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion with "
                                     "FP64 reliable updates, to 1e-10"),
+    "full32_single12": dict(kind_solve="full", dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="single12",
+                            desc="full-system solve M x = b (both parities) on 32^4 Haar, m=0.01: even-odd reduction "
+                                 "onto the mixed CG (FP32 recon-12 inner, FP64 reliable updates), full FP64 residual 1e-10"),
     "force32_fp64": dict(kind_solve="force", dims=(32, 32, 32, 32), mass=0.1, tol=1e-10,
                          desc="staggered fermion force on every link of a 32^4 Haar lattice from the CG's x and "
                               "y = D_oe x (m = 0.1), FP64"),
@@ -753,6 +756,137 @@ def run_gpu_wilson(args, wl):
     return out if rank == 0 else None
 
 
+def run_gpu_full(args, wl):
+    """Full-system solve M x = b on both parities (qcd_solve_full: even-odd reduction onto the CG,
+    odd half reconstructed, full FP64 residual |b - M x| / |b|). One step = qcd_load_links + the solve;
+    value = Dslash GFLOP/s (570 flop per output site of every half-lattice operator application:
+    those of the even CG plus the source b', and the two of the final full residual)."""
+    import torch
+
+    from paper_1311_2719_gb300 import inputs as I
+    from paper_1311_2719_gb300 import qcd as Q
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dims, mass, tol, inner = wl["dims"], wl["mass"], wl["tol"], wl["inner"]
+    prec_in, recon_in = PRECS[inner]
+    stream = torch.cuda.Stream()
+    lat = Q.Lattice(dims)
+    Vh = lat.Vh
+    U_np = I.make_links(dims, kind="haar", seed=1)
+    b_np = I.make_source(dims, seed=2)
+    U_host, b_host = torch.from_numpy(U_np).pin_memory(), torch.from_numpy(b_np).pin_memory()
+    U_dev, b_dev = U_host.to("cuda"), b_host.to("cuda")
+    x_dev = torch.zeros_like(b_dev)
+    x_host = torch.empty_like(b_host).pin_memory()
+    packed = {p: (lat.empty_bytes(Q.qcd_links_bytes(lat.handle, p, r)), r) for p, r in {(0, 18), (prec_in, recon_in)}}
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner, opts.recon_inner = prec_in, recon_in
+    ws = lat.empty_bytes(Q.qcd_workspace_bytes_full(lat.handle, opts))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(host_io=False, profile=False):
+        opts.profile = 1 if profile else 0
+        with torch.cuda.stream(stream):
+            if host_io:
+                U_dev.copy_(U_host, non_blocking=True)
+                b_dev.copy_(b_host, non_blocking=True)
+            for p, (buf, r) in packed.items():
+                Q.qcd_load_links(lat.handle, U_dev, buf, p, r, stream)
+            rc, info = Q.qcd_solve_full(lat.handle, x_dev, b_dev, mass, tol, 100000, opts, ws, stream=stream)
+            if host_io:
+                x_host.copy_(x_dev, non_blocking=True)
+        if rc != Q.QCD_OK:
+            raise RuntimeError(f"full solve failed: {Q.qcd_status_string(rc)} {info}")
+        return info
+
+    def timed(n, host_io=False, profile=False):
+        ms, infos = [], []
+        for _ in range(n):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step(host_io, profile))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    proc, cpath = _clock_sampler(uuid)
+    time.sleep(0.3)
+    ms, infos = timed(args.steps)
+    clocks = _clock_summary(proc, cpath)
+    _, infos_p = timed(max(1, min(args.steps, 2)), profile=True)
+    ms_e2e, infos_e2e = timed(args.steps, host_io=True)
+
+    def flops(i):
+        return FLOP_PER_SITE * Vh * (_half_dslash_count(i) + 3)
+
+    (t_ms, t_e2e), (f_all, f_e2e) = reduce_over_ranks([sum(ms), sum(ms_e2e)],
+                                                       [sum(flops(i) for i in infos), sum(flops(i) for i in infos_e2e)])
+    link_b, fld_b, x_b = {"double": (1152, 48, 48), "single18": (576, 24, 24), "single12": (384, 24, 24),
+                          "half12": (192, 16, 24), "df64": (1152, 48, 48)}[inner]
+    k1_b, k2_b = link_b + 2 * fld_b, link_b + fld_b + 2 * fld_b + x_b + fld_b + x_b
+    per_ms = sum(i["dslash_ms"] for i in infos_p) / sum(i["dslash_launches"] for i in infos_p)
+    alg = (k1_b + k2_b) / 2 * Vh
+    ach = alg / (per_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    out = {
+        "metric": METRIC, "value": round(f_all / (t_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[inner], "data": "synthetic (seeded Haar SU(3) links, Gaussian source)",
+        "config": {"workload": wl["desc"], "dims": list(dims), "mass": mass, "tol": tol, "inner": inner,
+                   "parallelism": f"replicas x{world} (no sharding)",
+                   "l2": "flushed before every step (512 MB write, outside the timed events)",
+                   "step": "qcd_load_links + qcd_solve_full (both parities, full FP64 residual)"},
+        "cg": {"iterations": infos[-1]["iterations"], "full_rel_residual": infos[-1]["true_rel_residual"],
+               "reliable_updates": infos[-1]["reliable_updates"], "time_to_solution_ms": round(t_ms / args.steps, 4)},
+        "roofline": {"bound": "hbm", "kernel": "dslash_kernel (K1+K2 launches of the even CG)", "achieved": round(ach, 1),
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                     "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": ncu_traffic(args.workload),
+                     "alg_bytes_per_launch": alg, "avg_launch_us": round(per_ms * 1e3, 3)},
+        "e2e": {"value": round(f_e2e / (t_e2e * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int((U_host.numel() + b_host.numel()) * 16), "d2h_bytes_per_step": int(x_host.numel() * 16),
+                "ms_per_step": round(t_e2e / args.steps, 4)},
+        "gpu_launches": int(sum(len(packed) + i["kernel_launches"] for i in infos)),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import staggered as So
+        t0 = time.perf_counter()
+        res = So.solve_full(U_np, b_np, dims, mass, tol, 6)
+        dt = time.perf_counter() - t0
+        # the oracle's full-lattice CG: 2 full D (= 4 half-lattice operators) per iteration, 1 for M^dagger b,
+        # 3 for the final residuals
+        f_cpu = FLOP_PER_SITE * Vh * (4 * res["iterations"] + 2 + 6)
+        out["cpu_baseline"] = {"value": round(f_cpu / dt / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                               "sample": f"FP64 numpy oracle full-lattice CG on the same {tuple(dims)} workload, first "
+                                         f"{res['iterations']} iterations + residuals ({dt:.1f} s)"}
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
 FORCE_FLOP_PER_LINK = 162  # U b (66) + a b^dagger (54) + coefficient (6) + i (W - W^dagger) (18) + trace removal (18)
 
 
@@ -1028,6 +1162,8 @@ def main():
         out = run_gpu_wilson(args, wl)
     elif wl.get("kind_solve") == "force":
         out = run_gpu_force(args, wl)
+    elif wl.get("kind_solve") == "full":
+        out = run_gpu_full(args, wl)
     else:
         out = run_gpu(args, wl)
     if out is not None:
