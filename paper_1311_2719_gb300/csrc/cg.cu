@@ -1,8 +1,8 @@
 // Conjugate gradient on the even-site normal operator A = m^2 - D_eo D_oe (the paper's congrad, §4).
 //
 // One iteration is three kernels, with every CG scalar kept on the device:
-//   K3  p = r + beta p,                       partial <p,p>    -> pp
-//   K1  ap = D_oe p            (fused store), partial <ap,ap>  -> alpha = rr / (<ap,ap> + m^2 pp)
+//   K3  p = r + beta p (a plain axpy)
+//   K1  ap = D_oe p            (fused store), partials <ap,ap>, <p,p> -> alpha = rr / (<ap,ap> + m^2 <p,p>)
 //   K2  t = D_eo ap; x += alpha p; r -= alpha (m^2 p - t), partial <r,r> -> beta, exit test
 // (the paper's order with its final "p = r + beta p" moved to the start of the next iteration;
 // the first K3 runs with beta = 0 and p = 0, giving p = r = b).

@@ -79,12 +79,12 @@ __global__ void __launch_bounds__(kSpreadBlockMax) cg_init_kernel(Geom g, const 
 }
 
 // ---------------------------------------------------------------- K3: p = r + beta p
+// A plain axpy: |p|^2 is summed by the next K1 (which reads p anyway), so K3 needs no grid reduction.
 template <class FieldT>
-__global__ void __launch_bounds__(kSpreadBlockMax) cg_p_kernel(int Vh, FieldT r, FieldT p, CgScalars* sc, double* partials) {
+__global__ void __launch_bounds__(kSpreadBlockMax) cg_p_kernel(int Vh, FieldT r, FieldT p, CgScalars* sc) {
   using T = typename FieldT::T;
   if (sc->done != kRunning) return;
   const T beta = (T)sc->beta;
-  typename Accum<T>::type part = 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Vh; k += gridDim.x * blockDim.x) {
     cvec3<T> rv = r.load(k), pv = p.load(k);
 #pragma unroll
@@ -93,19 +93,18 @@ __global__ void __launch_bounds__(kSpreadBlockMax) cg_p_kernel(int Vh, FieldT r,
       pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
     }
     p.store(k, pv);
-    accum(part, norm2(pv));
   }
-  double red[1] = {(double)part};
-  double tot[1];
-  if (grid_sum_last_block<1>(red, partials, &sc->counter[1], tot) && threadIdx.x == 0) sc->pp = tot[0];
 }
 
 // ---------------------------------------------------------------- K1 epilogue: ap = D_oe p
+// Besides |ap|^2 (odd sites) it sums |p|^2 over the even site with the same index k, so that every
+// even site is counted once: alpha = rr / (|D_oe p|^2 + m^2 |p|^2) from one launch.
 template <class FieldT>
 struct EpiAp {
-  static constexpr int NV = 1;
+  static constexpr int NV = 2;
   static constexpr bool kPrefetch = false;
   FieldT ap;
+  FieldT p;  // the even field the operator reads
   CgScalars* sc;
   double* partials;
   __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
@@ -113,12 +112,14 @@ struct EpiAp {
   __device__ __forceinline__ void site(int k, cvec3<T>& acc, A* red) const {
     ap.store(k, acc);
     accum(red[0], norm2(acc));
+    accum(red[1], norm2(p.load(k)));
   }
   template <class A>
   __device__ __forceinline__ void finish(A* red) const {
-    double v[1] = {(double)red[0]}, tot[1];
-    if (grid_sum_last_block<1>(v, partials, &sc->counter[2], tot) && threadIdx.x == 0) {
-      const double d = tot[0] + sc->m2 * sc->pp;  // <p, A p> = |D_oe p|^2 + m^2 |p|^2
+    double v[2] = {(double)red[0], (double)red[1]}, tot[2];
+    if (grid_sum_last_block<2>(v, partials, &sc->counter[2], tot) && threadIdx.x == 0) {
+      sc->pp = tot[1];
+      const double d = tot[0] + sc->m2 * tot[1];  // <p, A p> = |D_oe p|^2 + m^2 |p|^2
       const double alpha = sc->rr / d;
       if (!finite_pos(d) || !isfinite(alpha)) {
         sc->done = kBreakdown;
@@ -456,14 +457,15 @@ struct CgRunner {
     else dslash_kernel<LinksT, InT, Epi, 1><<<grid, block, 0, st>>>(g, U, in, out_par, epi);
   }
 
-  // One CG iteration (K3, K1, K2). With `ev` (4 events) the two operator launches are bracketed.
+  // One CG iteration (K3 p = r + beta p; K1 ap = D_oe p with |ap|^2 and |p|^2; K2 D_eo ap and the
+  // x, r update with |r|^2). With `ev` (4 events) the two operator launches are bracketed.
   int iteration(cudaEvent_t* ev = nullptr) {
     auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
     FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh), ap = make_field<PREC>(w.ap, g.Vh);
     XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
-    cg_p_kernel<<<grid, block, 0, st>>>(g.Vh, r, p, w.sc, w.partials);
+    cg_p_kernel<<<grid, block, 0, st>>>(g.Vh, r, p, w.sc);
     if (ev) QCD_CUDA(cudaEventRecord(ev[0], st));
-    op(U, p, QCD_ODD, EpiAp<FieldT>{ap, w.sc, w.partials});
+    op(U, p, QCD_ODD, EpiAp<FieldT>{ap, p, w.sc, w.partials});
     if (ev) QCD_CUDA(cudaEventRecord(ev[1], st));
     if (ev) QCD_CUDA(cudaEventRecord(ev[2], st));
     op(U, ap, QCD_EVEN, EpiUpdate<FieldT, XFieldT>{p, r, x, w.sc, w.partials});
