@@ -452,13 +452,17 @@ def run_gpu_batched(args, wl):
             ms.append(e0.elapsed_time(e1))
         return ms, outs
 
+    tuned = None
     if args.tune:
         with torch.cuda.stream(stream):
             load_links()
             if wl["kind_solve"] == "mrhs":
-                Q.qcd_tune_mrhs(lats[0].handle, nrhs, x_dev[0], b_dev[0], masses[0], opts, ws, stream=stream)
+                tuned = {"rhs_block": Q.qcd_tune_mrhs(lats[0].handle, nrhs, x_dev[0], b_dev[0], masses[0], opts, ws,
+                                                      stream=stream)}
             else:
-                Q.qcd_tune_batched([l.handle for l in lats], x_dev, b_dev, masses, tol, 100000, opts, ws, stream=stream)
+                c, blk = Q.qcd_tune_batched([l.handle for l in lats], x_dev, b_dev, masses, tol, 100000, opts, ws,
+                                            stream=stream)
+                tuned = {"cluster_size": c, "block_size": blk}
         torch.cuda.synchronize()
     for _ in range(args.warmup):
         step()
@@ -515,6 +519,7 @@ def run_gpu_batched(args, wl):
                "speedup_vs_plain_fp64_gpu_cg": round(t_fp64 / t_batched, 3)},
         "gpu_launches": int(sum(o[2] for o in outs)),
         "clocks": clocks,
+        "tuned": tuned,
     }
     # roofline. Algorithmic bytes per output site of a half-lattice operator at the inner precision:
     # links once per launch (shared by every RHS), and per RHS K1 = p in + ap out, K2 = ap in, p in,

@@ -69,8 +69,15 @@ __global__ void __launch_bounds__(kBlock) cg_p_mrhs_kernel(int Vh, FieldT r_all,
 }
 
 // ---------------------------------------------------------------- operator kernel with per-RHS epilogue
+// resident blocks per SM of the multi-RHS operator: 4 (at most 128 registers) for the FP32-arithmetic
+// register blocks up to 4 RHS, the compiler's own choice otherwise
+template <class LinksT, int RB>
+struct MrhsMinBlocks {
+  static constexpr int value = (sizeof(typename LinksT::T) == 4 && RB <= 4) ? 4 : 0;
+};
+
 template <class LinksT, class FieldT, int RB, class Epi>
-__global__ void __launch_bounds__(kBlock) dslash_mrhs_cg_kernel(Geom g, LinksT U, FieldT in, int nrhs, int out_par,
+__global__ void __launch_bounds__(kBlock, MrhsMinBlocks<LinksT, RB>::value) dslash_mrhs_cg_kernel(Geom g, LinksT U, FieldT in, int nrhs, int out_par,
                                                                 Epi epi) {
   using T = typename LinksT::T;
   const int r0 = blockIdx.y * RB;
@@ -263,12 +270,19 @@ struct MrhsRunner {
   }
 };
 
-// Default RHS block (when nothing is tuned): at most 4. Measured on GB300, 16 right-hand sides
-// in registers take 254 registers per thread, leave 2 blocks per SM and run at a tenth of the
-// memory bandwidth; qcd_tune_mrhs can still choose 8 or 16 where they pay.
-inline int default_rhs_block(int prec, int R) {
-  const int cap = 4;
+// Default RHS block (when nothing is tuned). Links that fit in half of L2 are read from L2 by
+// every grid row, so register blocking buys nothing and costs registers: 1 (measured on GB300 at
+// 24^4 x 16 RHS, FP32 recon-12, links 64 MB: 276 ms per solve against 303 ms with 4). Larger link
+// fields would be streamed from DRAM once per row: up to 4 RHS per row. (16 RHS in registers take
+// 254 registers per thread and run at a tenth of the bandwidth; qcd_tune_mrhs can still choose
+// 8 or 16 where they pay.)
+inline int default_rhs_block(int prec, int R, size_t links_bytes) {
   (void)prec;
+  int dev = 0, l2 = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
+      l2 > 0 && links_bytes * 2 <= (size_t)l2)
+    return 1;
+  const int cap = 4;
   int rb = 1;
   while (rb * 2 <= R && rb * 2 <= cap) rb *= 2;
   if (rb < R && rb * 2 <= cap) rb *= 2;  // one partially filled block beats two passes
@@ -289,7 +303,8 @@ int mrhs_typed(qcd_lattice* lat, int R, void* x, const void* b, double mass, dou
   if ((PREC == QCD_PREC_DOUBLE || PREC == QCD_PREC_DF64) && M.rb > 4) M.rb = 4;
   if (M.rb <= 0) {
     std::vector<int> tuned;
-    M.rb = tune_lookup(mrhs_key(lat, PREC, RECON, R), &tuned) ? tuned[0] : default_rhs_block(PREC, R);
+    M.rb = tune_lookup(mrhs_key(lat, PREC, RECON, R), &tuned) ? tuned[0]
+                                                                : default_rhs_block(PREC, R, links_bytes(PREC, RECON, lat->Vh));
   }
   const bool mixed = PREC != QCD_PREC_DOUBLE;
   const size_t canon_bytes = (size_t)lat->V * 3 * sizeof(double2);
