@@ -69,6 +69,14 @@ WORKLOADS = {
                                inner="single18", nrhs=1,
                                desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion with "
                                     "FP64 reliable updates, to 1e-10"),
+    "wilson32c64_single_df64": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
+                                    inner="single18", nrhs=1, outer="df64", traffic_key="wilson32c64_single",
+                                    desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion "
+                                         "with df64 reliable updates and solution, to 1e-10"),
+    "wilson32c64_8rhs_df64": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
+                                  inner="single18", nrhs=8, outer="df64", traffic_key="wilson32c64_8rhs",
+                                  desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, 8 RHS in one multi-RHS CGNR on "
+                                       "M^dagger M: FP32 recursion with df64 reliable updates and solution, to 1e-10"),
     "full32_single12": dict(kind_solve="full", dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="single12",
                             desc="full-system solve M x = b (both parities) on 32^4 Haar, m=0.01: even-odd reduction "
                                  "onto the mixed CG (FP32 recon-12 inner, FP64 reliable updates), full FP64 residual 1e-10"),
@@ -578,9 +586,10 @@ def _wilson_dw_count(info):
 
 def run_gpu_wilson(args, wl):
     """Wilson CGNR (M = 1 - kappa D_W on the full lattice) on nrhs right-hand sides in one multi-RHS
-    solve. One step = pack the links at FP64 and FP32 and run the mixed CGNR on every RHS; value =
-    Wilson D_W GFLOP/s inside the solve (1320 flop per site per D_W application). The same RHS solved
-    by plain FP64 CGNR on the GPU are timed beside, with the speedup."""
+    solve. One step = pack the links at the outer precision (the workload's "outer": FP64 or df64)
+    and at FP32, and run the mixed CGNR on every RHS; value = Wilson D_W GFLOP/s inside the solve
+    (1320 flop per site per D_W application). The same RHS solved with the other outer precision and
+    by plain FP64 CGNR on the GPU are timed beside."""
     import numpy as np
     import torch
 
@@ -603,21 +612,26 @@ def run_gpu_wilson(args, wl):
     b_dev = b_host.to("cuda")
     x_dev = torch.zeros_like(b_dev)
     x_host = torch.empty_like(b_host).pin_memory()
-    bufs = {p: lat.empty_bytes(Q.qcd_wilson_links_bytes(lat.handle, p)) for p in (0, 1)}
+    outer = Q.PREC_NAMES[wl.get("outer", "double")]
+    other = Q.QCD_PREC_DF64 if outer == Q.QCD_PREC_DOUBLE else Q.QCD_PREC_DOUBLE
+    bufs = {p: lat.empty_bytes(Q.qcd_wilson_links_bytes(lat.handle, p)) for p in (0, 1, 3)}
     opts = Q.qcd_solver_opts_default()
-    ws = {1: lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))}  # FP32 inner (the default)
+    opts.prec_inner, opts.prec_outer = 1, outer
+    ws = {1: lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))}  # FP32 inner, either outer
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     launches_links = 2
 
-    def solve(prec, host_io=False, profile=False):
-        opts.prec_inner = prec
+    def solve(prec, host_io=False, profile=False, hi=None):
+        # one step packs the links the solve reads: the inner precision and the outer one
+        hi = (outer if hi is None else hi) if prec != 0 else 0
+        opts.prec_inner, opts.prec_outer = prec, hi
         opts.profile = 1 if profile else 0
         with torch.cuda.stream(stream):
             if host_io:
                 U_dev.copy_(U_host, non_blocking=True)
                 b_dev.copy_(b_host, non_blocking=True)
-            for p, buf in bufs.items():
-                Q.qcd_wilson_load_links(lat.handle, U_dev, buf, p, stream)
+            for p in sorted({prec, hi}):
+                Q.qcd_wilson_load_links(lat.handle, U_dev, bufs[p], p, stream)
             rc, infos = Q.qcd_wilson_cgnr_mrhs(lat.handle, R, x_dev, b_dev, kappa, tol, 100000, opts, ws[prec],
                                                stream=stream)
             if host_io:
@@ -626,14 +640,14 @@ def run_gpu_wilson(args, wl):
             raise RuntimeError(f"Wilson CGNR failed: {Q.qcd_status_string(rc)} {infos}")
         return infos
 
-    def timed(prec, n, host_io=False, profile=False):
+    def timed(prec, n, host_io=False, profile=False, hi=None):
         ms, runs = [], []
         for _ in range(n):
             flush.fill_(1)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            runs.append(solve(prec, host_io, profile))
+            runs.append(solve(prec, host_io, profile, hi))
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -660,13 +674,21 @@ def run_gpu_wilson(args, wl):
         dist.barrier()
     ms_prof, runs_prof = timed(1, max(1, min(args.steps, 3)), profile=True)
     ms_e2e, runs_e2e = timed(1, args.steps, host_io=True)
+    ms_oth, runs_oth = None, None
+    if not args.no_variant:
+        solve(1, hi=other)
+        ms_oth, runs_oth = timed(1, max(1, min(args.steps, 2)), hi=other)
     del ws[1]
-    opts.prec_inner = 0
+    opts.prec_inner, opts.prec_outer = 0, 0
     ws[0] = lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))
     solve(0)
     ms64, runs64 = timed(0, max(1, min(args.steps, 2)))
 
     # operator kernels alone (CUDA events on the launching stream, L2 flushed before each)
+    with torch.cuda.stream(stream):
+        for p in (0, 1, 3):
+            Q.qcd_wilson_load_links(lat.handle, U_dev, bufs[p], p, stream)
+
     def op_time(prec, nrhs, reps=5):
         fb = Q.qcd_wilson_field_bytes(lat.handle, prec)
         fin, fout = lat.empty_bytes(nrhs * fb), lat.empty_bytes(nrhs * fb)
@@ -689,6 +711,7 @@ def run_gpu_wilson(args, wl):
         return statistics.median(t)
 
     t_op64 = op_time(0, 1)
+    t_opdf = op_time(3, 1)
     t_op32 = op_time(1, 1)
     t_op32_r = op_time(1, R) if R > 1 else t_op32
 
@@ -720,11 +743,14 @@ def run_gpu_wilson(args, wl):
         "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_mixed, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (FP64 reliable updates)", "data": "synthetic (seeded Haar SU(3) links, Gaussian spinors)",
+        "dtype": "f32 (FP64 reliable updates)" if outer == 0 else "f32 (df64 reliable updates)",
+        "data": "synthetic (seeded Haar SU(3) links, Gaussian spinors)",
         "config": {"workload": wl["desc"], "dims": list(dims), "kappa": kappa, "tol": tol, "nrhs": R,
                    "parallelism": f"replicas x{world} (no sharding)",
                    "l2": "flushed before every step (512 MB write, outside the timed events)",
-                   "step": "qcd_wilson_load_links (FP64 + FP32) + qcd_wilson_cgnr_mrhs"},
+                   "outer": wl.get("outer", "double"),
+                   "step": "qcd_wilson_load_links (" + ("FP64" if outer == 0 else "df64") +
+                           " + FP32) + qcd_wilson_cgnr_mrhs"},
         "cg": {"iterations": [i["iterations"] for i in runs[-1]],
                "reliable_updates": [i["reliable_updates"] for i in runs[-1]],
                "max_true_rel_residual": max(i["true_rel_residual"] for i in runs[-1]),
@@ -734,7 +760,8 @@ def run_gpu_wilson(args, wl):
         "roofline": {"bound": "hbm", "kernel": "wilson_mrhs_kernel (CGNR K1+K2 launches, FP32)",
                      "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
-                     "traffic": ncu_traffic(args.workload), "alg_bytes_per_launch": round(alg / d_launches),
+                     "traffic": ncu_traffic(wl.get("traffic_key", args.workload)),
+                     "alg_bytes_per_launch": round(alg / d_launches),
                      "alg_bytes_per_site": {"links_per_launch": link_b, "k1_per_rhs": k1_b, "k2_per_rhs": k2_b},
                      "avg_launch_us": round(d_ms / d_launches * 1e3, 3)},
         "operator_alone": {
@@ -747,7 +774,21 @@ def run_gpu_wilson(args, wl):
                                "alg_bytes_per_site": 288 + 192 * R},
             "fp64_M_1rhs": {"us": round(t_op64 * 1e3, 2), "tflops": round(op_flops / (t_op64 * 1e-3) / 1e12, 4),
                             "frac_fp64_peak": round(op_flops / (t_op64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
-                            "note": "FP64 D_W is FP64-pipe bound on GB300 (1320 flop vs 960 B per site)"}},
+                            "note": "FP64 D_W is FP64-pipe bound on GB300 (1320 flop vs 960 B per site)"},
+            "df64_M_1rhs": {"us": round(t_opdf * 1e3, 2),
+                            "gbs": round(960 * V / (t_opdf * 1e-3) / 1e9, 1),
+                            "frac_hbm": round(960 * V / (t_opdf * 1e-3) / 1e9 / hbm_peak, 4),
+                            "alg_bytes_per_site": 960,
+                            "speedup_vs_fp64_M": round(t_op64 / t_opdf, 3),
+                            "note": "df64 D_W: FP32 pairs on the FP32 pipes, 960 B per site like FP64"}},
+        "other_outer_precision": None if ms_oth is None else {
+            "outer": "df64" if other == Q.QCD_PREC_DF64 else "double",
+            "ms_per_step": round(sum(ms_oth) / len(ms_oth), 4),
+            "value": round(flops_of(runs_oth) / (sum(ms_oth) * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+            "iterations": [i["iterations"] for i in runs_oth[-1]],
+            "reliable_updates": [i["reliable_updates"] for i in runs_oth[-1]],
+            "max_true_rel_residual": max(i["true_rel_residual"] for i in runs_oth[-1]),
+            "time_ratio_vs_headline": round((sum(ms_oth) / len(ms_oth)) / t_mixed, 3)},
         "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": int(U_host.numel() * 16 + b_host.numel() * 16),
                 "d2h_bytes_per_step": int(x_host.numel() * 16), "ms_per_step": round(total_ms_e2e / args.steps, 4)},
         "gpu_launches": int(sum(launches_links + infos[0]["kernel_launches"] for infos in runs)),

@@ -95,6 +95,11 @@ typedef struct {
   long long wait_cycles; /* limit of a device-side wait on an mbarrier, in SM clock cycles (the
                             staged operator); 0 = 4e9 (about 2 s). On expiry the solve returns
                             QCD_ERR_TIMEOUT.                                                    */
+  int prec_outer;        /* Wilson CGNR with prec_inner = SINGLE: precision of the solution
+                            accumulator, the reliable updates and the confirming residual:
+                            QCD_PREC_DOUBLE (default) or QCD_PREC_DF64 (the same 16 bytes per
+                            complex, 48-bit significand, computed on the FP32 pipes); the
+                            staggered solvers ignore it                                        */
 } qcd_solver_opts;
 
 /* What a solve reports. */
@@ -133,6 +138,12 @@ QCD_API int qcd_lattice_device(const qcd_lattice* lat);
 
 /* ---- sizes ------------------------------------------------------------------------------------ */
 
+/* Bytes from ptr to the end of the device allocation that holds it, as the argument checks measure
+ * it; 0 when unknown (not device memory, no driver, or memory of the virtual-memory or
+ * stream-ordered allocators, whose mapped ranges the checks do not measure). Every entry point
+ * returns QCD_ERR_INVALID_ARG, before any device work, for a buffer whose known span is shorter
+ * than what the call reads or writes (e.g. a workspace sized for other options). */
+QCD_API size_t qcd_device_span_bytes(const void* ptr);
 /* Bytes of one packed single-parity field at `prec` (0 on a bad argument). */
 QCD_API size_t qcd_field_bytes(const qcd_lattice* lat, int prec);
 /* Bytes of the packed gauge field at (prec, recon). Supported: DOUBLE/18, SINGLE/18, SINGLE/12,
@@ -279,7 +290,9 @@ QCD_API int qcd_fermion_force(const qcd_lattice* lat, void* force_dev, const voi
  *   D_W psi(n) = sum_mu [ (1 - gamma_mu) U_mu(n) psi(n+mu) + (1 + gamma_mu) U_mu(n-mu)^dagger psi(n-mu) ]
  *   M = 1 - kappa D_W,  M^dagger = gamma5 M gamma5,  gamma5 = diag(1, 1, -1, -1).
  * Canonical spinor field: complex128[V][4][3] (spin, colour); packed field: the library's
- * structure-of-arrays layout over all V sites (qcd_wilson_field_bytes). Precisions: DOUBLE, SINGLE. */
+ * structure-of-arrays layout over all V sites (qcd_wilson_field_bytes). Precisions: DOUBLE, SINGLE
+ * and DF64 (float4 {re.hi, re.lo, im.hi, im.lo} per complex, 16 bytes like DOUBLE; the multi-RHS
+ * operator takes DOUBLE and SINGLE only). */
 enum { QCD_WILSON_DSLASH = 0, QCD_WILSON_M = 1, QCD_WILSON_MDAG = 2 };
 QCD_API size_t qcd_wilson_field_bytes(const qcd_lattice* lat, int prec);
 QCD_API size_t qcd_wilson_links_bytes(const qcd_lattice* lat, int prec);
@@ -302,13 +315,18 @@ QCD_API int qcd_wilson_op_mrhs(const qcd_lattice* lat, void* out_dev, const void
 /* Bytes of the device workspace qcd_wilson_cgnr (nrhs = 1) or qcd_wilson_cgnr_mrhs needs for these
  * options; 0 on a bad argument (nrhs outside [1, 16], unsupported precision). */
 QCD_API size_t qcd_wilson_workspace_bytes(const qcd_lattice* lat, const qcd_solver_opts* opts, int nrhs);
-/* CGNR: M^dagger M x = M^dagger b to |M^dagger b - M^dagger M x| / |M^dagger b| <= tol (recomputed in FP64,
- * returned in info->true_rel_residual); canonical spinor fields complex128[V][4][3].
+/* CGNR: M^dagger M x = M^dagger b to |M^dagger b - M^dagger M x| / |M^dagger b| <= tol (recomputed at
+ * the outer precision, returned in info->true_rel_residual); canonical spinor fields
+ * complex128[V][4][3].
  * opts->prec_inner = SINGLE runs the recursion in FP32 with reliable updates (opts->reliable_delta,
- * opts->reliable_interval; links loaded at both precisions): each update folds the FP32 increment
- * into the FP64 solution, recomputes the true residual b - M x in FP64 and restarts the recursion
- * from M^dagger (b - M x); a RHS stops only after the full FP64 residual of the normal equations
- * confirms the tolerance. DOUBLE runs plain FP64 CGNR, confirmed the same way. Synchronises `stream`.
+ * opts->reliable_interval): each update folds the FP32 increment into the high-precision solution,
+ * recomputes the true residual b - M x at that precision and restarts the recursion from
+ * M^dagger (b - M x); a RHS stops only after the full high-precision residual of the normal
+ * equations confirms the tolerance. The high precision is opts->prec_outer: DOUBLE (FP64) or DF64
+ * (about 1e-14 relative rounding; on GB300 its operator runs on the FP32 pipes, several times
+ * faster than the FP64 pipe). Links must be loaded at prec_inner and at prec_outer. DOUBLE inner
+ * precision runs plain FP64 CGNR, confirmed the same way (prec_outer must then be DOUBLE).
+ * Synchronises `stream`.
  * Returns QCD_ERR_NOT_CONVERGED when max_iter runs out, QCD_ERR_BREAKDOWN on a non-finite or
  * non-positive CG scalar. */
 QCD_API int qcd_wilson_cgnr(qcd_lattice* lat, void* x_dev, const void* b_dev, double kappa, double tol, int max_iter,

@@ -18,6 +18,7 @@ namespace qcd {
 
 int launch_mdagm(const qcd_lattice*, void*, const void*, double, int, void*, cudaStream_t);
 void set_error(const char* fmt, ...);
+size_t device_span(const void* p);
 
 constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB: one packed odd field
 constexpr int kMaxDevices = 64;
@@ -72,6 +73,14 @@ extern "C" int qcd_mdagm_noalloc(const qcd_lattice* lat, void* out_dev, const vo
   if (!lat->links[prec].ptr || !lat->links[prec].recon) {
     set_error("no links loaded for precision %d (call qcd_load_links first)", prec);
     return QCD_ERR_NO_LINKS;
+  }
+  for (const void* p : {(const void*)out_dev, in_dev}) {
+    const size_t have = device_span(p);
+    if (have && have < need) {
+      set_error("qcd_mdagm_noalloc: a field buffer has %zu bytes to the end of its device allocation, %zu needed",
+                have, need);
+      return QCD_ERR_INVALID_ARG;
+    }
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -34,7 +34,8 @@ struct qcd_lattice {
   int tbc;
   int device;
   qcd::LinkSet links[4];  // indexed by precision
-  void* wilson_links[2] = {nullptr, nullptr};  // Wilson operator links, FP64 / FP32 (caller-owned)
+  void* wilson_links[4] = {nullptr, nullptr, nullptr, nullptr};  // Wilson operator links by precision
+                                                                 // (FP64, FP32, -, df64; caller-owned)
 };
 
 namespace qcd {

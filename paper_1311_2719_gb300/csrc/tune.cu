@@ -70,6 +70,10 @@ int run_cg_mrhs(qcd_lattice*, int, void*, const void*, double, double, int, cons
                 qcd_solve_info*, cudaStream_t);
 int run_cg_batched(int, qcd_lattice* const*, void* const*, const void* const*, void* const*, const double*, double, int,
                    const qcd_solver_opts&, void*, qcd_solve_info*, cudaStream_t);
+int check_mrhs_args(const qcd_lattice*, int, void*, const void*, void*, double, double, int, const qcd_solver_opts*,
+                    void*, qcd_solver_opts&);
+int check_batched_args(int, qcd_lattice* const[], void* const[], const void* const[], void* const[], const double[],
+                       double, int, const qcd_solver_opts*, void*, qcd_solver_opts&);
 
 }  // namespace qcd
 
@@ -102,17 +106,12 @@ int qcd_tune_load(const char* cache_path) {
 int qcd_tune_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, double mass,
                   const qcd_solver_opts* opts, void* workspace_dev, const char* cache_path, int* best_rhs_block,
                   void* stream) {
-  if (!lat || !best_rhs_block || nrhs < 1 || nrhs > kMaxRhs) {
-    set_error("bad argument to qcd_tune_mrhs");
+  if (!best_rhs_block) {
+    set_error("best_rhs_block is NULL");
     return QCD_ERR_INVALID_ARG;
   }
   qcd_solver_opts o;
-  qcd_solver_opts_default(&o);
-  if (opts) o = *opts;
-  if (!lat->links[o.prec_inner].ptr || !lat->links[QCD_PREC_DOUBLE].ptr) {
-    set_error("links for the inner precision and FP64 must be loaded before tuning");
-    return QCD_ERR_NO_LINKS;
-  }
+  if (int rc = check_mrhs_args(lat, nrhs, x_dev, b_dev, nullptr, mass, 1e-14, 24, opts, workspace_dev, o)) return rc;
   o.profile = 1;
   const int cands[] = {1, 2, 4, 8, 16};
   double best_us = 1e300;
@@ -146,18 +145,12 @@ int qcd_tune_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, do
 int qcd_tune_batched(int n, qcd_lattice* const lats[], void* const x[], const void* const b[], const double mass[],
                      double tol, int max_iter, const qcd_solver_opts* opts, void* workspace_dev,
                      const char* cache_path, int* best_cluster, int* best_block, void* stream) {
-  if (n < 1 || !lats || !x || !b || !mass || !best_cluster || !best_block || !workspace_dev) {
-    set_error("bad argument to qcd_tune_batched");
+  if (!best_cluster || !best_block) {
+    set_error("best_cluster and best_block must not be NULL");
     return QCD_ERR_INVALID_ARG;
   }
   qcd_solver_opts o;
-  qcd_solver_opts_default(&o);
-  if (opts) o = *opts;
-  for (int i = 0; i < n; ++i)
-    if (!lats[i] || !lats[i]->links[o.prec_inner].ptr || !lats[i]->links[QCD_PREC_DOUBLE].ptr) {
-      set_error("lattice %d: links for the inner precision and FP64 must be loaded before tuning", i);
-      return QCD_ERR_NO_LINKS;
-    }
+  if (int rc = check_batched_args(n, lats, x, b, nullptr, mass, tol, max_iter, opts, workspace_dev, o)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   QCD_CUDA(cudaEventCreate(&e0));

@@ -1,6 +1,6 @@
 // Wilson fermions (the paper's second program, §2/§6): the hopping term D_W on the full lattice,
 // M = 1 - kappa D_W, M^dagger = gamma5 M gamma5, and CGNR (CG on M^dagger M x = M^dagger b) with
-// FP64 reliable updates when the recursion runs in FP32.
+// FP64 (or df64) reliable updates when the recursion runs in FP32.
 //
 // Spin projection: (1 -+ gamma_mu)/2 are rank-2 projectors. In the DeGrand-Rossi basis every
 // gamma_mu has one non-zero entry per row, ph(r) in {+-1, +-i} at column col(r), with col(r) in
@@ -109,6 +109,34 @@ struct WField<QCD_PREC_SINGLE> {
   __host__ __device__ WField at(int r) const { return {p + (size_t)r * 6 * V, V}; }
 };
 
+// df64: float4 [12][V] {re.hi, re.lo, im.hi, im.lo}, the 16 bytes per complex of FP64. The
+// mixed CGNR can keep its solution accumulator, b, M^dagger b and the reliable-update residual in
+// this form: the operator on them then runs on the FP32 pipes instead of the FP64 pipe.
+template <>
+struct WField<QCD_PREC_DF64> {
+  using T = df64;
+  float4* p;
+  int V;
+  __device__ __forceinline__ spinor<df64> load(int i) const {
+    spinor<df64> v;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const float4 d = __ldg(p + (size_t)q * V + i);
+      v.s[q / 3].c[q % 3] = {df64(d.x, d.y), df64(d.z, d.w)};
+    }
+    return v;
+  }
+  __device__ __forceinline__ void store(int i, const spinor<df64>& v) const {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const cplx<df64> c = v.s[q / 3].c[q % 3];
+      p[(size_t)q * V + i] = make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo);
+    }
+  }
+  static size_t bytes(long long V) { return (size_t)V * 12 * sizeof(float4); }
+  __host__ __device__ WField at(int r) const { return {p + (size_t)r * 12 * V, V}; }
+};
+
 // links [mu][9][V], zeta folded into the t-links of the last time slice (no staggered phases)
 template <int PREC>
 struct WLinks;
@@ -147,13 +175,39 @@ struct WLinks<QCD_PREC_SINGLE> {
   static size_t bytes(long long V) { return (size_t)4 * 9 * V * sizeof(float2); }
 };
 
+template <>
+struct WLinks<QCD_PREC_DF64> {
+  using T = df64;
+  const float4* p;  // [mu][9][V] {re.hi, re.lo, im.hi, im.lo}
+  int V;
+  __device__ __forceinline__ su3<df64> load(int mu, int i) const {
+    su3<df64> U;
+    const float4* b = p + (size_t)mu * 9 * V + i;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float4 d = __ldg(b + (size_t)e * V);
+      U.e[e / 3][e % 3] = {df64(d.x, d.y), df64(d.z, d.w)};
+    }
+    return U;
+  }
+  static size_t bytes(long long V) { return (size_t)4 * 9 * V * sizeof(float4); }
+};
+
 size_t wfield_bytes(int prec, long long V) {
-  return prec == QCD_PREC_DOUBLE ? WField<QCD_PREC_DOUBLE>::bytes(V)
-                                 : (prec == QCD_PREC_SINGLE ? WField<QCD_PREC_SINGLE>::bytes(V) : 0);
+  switch (prec) {
+    case QCD_PREC_DOUBLE: return WField<QCD_PREC_DOUBLE>::bytes(V);
+    case QCD_PREC_SINGLE: return WField<QCD_PREC_SINGLE>::bytes(V);
+    case QCD_PREC_DF64: return WField<QCD_PREC_DF64>::bytes(V);
+    default: return 0;
+  }
 }
 size_t wlinks_bytes(int prec, long long V) {
-  return prec == QCD_PREC_DOUBLE ? WLinks<QCD_PREC_DOUBLE>::bytes(V)
-                                 : (prec == QCD_PREC_SINGLE ? WLinks<QCD_PREC_SINGLE>::bytes(V) : 0);
+  switch (prec) {
+    case QCD_PREC_DOUBLE: return WLinks<QCD_PREC_DOUBLE>::bytes(V);
+    case QCD_PREC_SINGLE: return WLinks<QCD_PREC_SINGLE>::bytes(V);
+    case QCD_PREC_DF64: return WLinks<QCD_PREC_DF64>::bytes(V);
+    default: return 0;
+  }
 }
 
 // ---------------------------------------------------------------- geometry (full lattice)
@@ -233,6 +287,10 @@ __device__ __forceinline__ spinor<typename LinksT::T> wilson_hop(const Geom& g, 
 // flight, which the latency-bound kernel needs more than a fifth and sixth block.
 template <typename T>
 struct WMinBlocks { static constexpr int value = 4; };
+// df64: a spinor accumulator of 48 FP32 pairs does not fit 128 registers without spills; 3 blocks
+// (168 registers) keep 12 warps per SM on the FP32 pipes.
+template <>
+struct WMinBlocks<df64> { static constexpr int value = 3; };
 
 template <class LinksT, class FieldT, bool G5IN, class Epi>
 __global__ void __launch_bounds__(kBlock, WMinBlocks<typename LinksT::T>::value) wilson_kernel(Geom g, int V, LinksT U, FieldT in, Epi epi) {
@@ -471,23 +529,23 @@ struct WEpiUpdate {
   }
 };
 
-// FP64 residual of the normal equations: res = rhs - M^dagger t (t = M x); r_lo <- res; |res|^2.
-// Used at start-up (x = 0: res = rhs), for reliable updates and for the final report.
-template <class FieldT, bool FINAL>
+// Residual of the normal equations at the high precision (FP64 or df64, HiT): res = rhs -
+// M^dagger t (t = M x); r_lo <- res; |res|^2. Used for the convergence check and the final report.
+template <class HiT, class FieldT, bool FINAL>
 struct WEpiResidual {
   static constexpr int NV = 1;
-  WField<QCD_PREC_DOUBLE> t, rhs;
+  HiT t, rhs;
   FieldT r_lo;
   double kappa;
   CgScalars* sc;
   double* partials;
   __device__ __forceinline__ bool skip() const { return false; }
-  template <class A>
-  __device__ __forceinline__ void site(int i, spinor<double>& acc, A* red) const {
+  template <class TH, class A>
+  __device__ __forceinline__ void site(int i, spinor<TH>& acc, A* red) const {
     using T = typename FieldT::T;
-    const spinor<double> s = m_combine<WField<QCD_PREC_DOUBLE>, true>(t, i, acc, kappa);
-    const spinor<double> b = rhs.load(i);
-    spinor<double> res;
+    const spinor<TH> s = m_combine<HiT, true>(t, i, acc, (TH)kappa);
+    const spinor<TH> b = rhs.load(i);
+    spinor<TH> res;
     spinor<T> rl;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -497,7 +555,7 @@ struct WEpiResidual {
         rl.s[q].c[a] = {(T)res.s[q].c[a].re, (T)res.s[q].c[a].im};
       }
     if (!FINAL) r_lo.store(i, rl);
-    red[0] += norm2(res);
+    accum(red[0], norm2(res));
   }
   template <class A>
   __device__ __forceinline__ void finish(A* red) const {
@@ -520,24 +578,24 @@ struct WEpiResidual {
 };
 
 // Reliable update of the mixed recursion, in two launches:
-//   (1) FP64: s = b - M x_hi, the true residual of M x = b (where the cancellation happens), stored
-//       at the inner precision;
+//   (1) high precision (FP64 or df64): s = b - M x_hi, the true residual of M x = b (where the
+//       cancellation happens), stored at the inner precision;
 //   (2) inner precision: r_lo = M^dagger s, |r_lo|^2 and the restart of the recursion.
 // The error of (2) is relative to the current residual (rounding of order eps_inner * cond(M)), the
-// same order as storing r_lo at the inner precision; convergence is only declared after the full FP64
-// residual of the normal equations (WEpiResidual) confirms it.
-template <class FieldT>
+// same order as storing r_lo at the inner precision; convergence is only declared after the
+// high-precision residual of the normal equations (WEpiResidual) confirms it.
+template <class HiT, class FieldT>
 struct WEpiSysResidual {
   static constexpr int NV = 0;
-  WField<QCD_PREC_DOUBLE> x, b;
+  HiT x, b;
   FieldT s_lo;
   double kappa;
   __device__ __forceinline__ bool skip() const { return false; }
-  template <class A>
-  __device__ __forceinline__ void site(int i, spinor<double>& acc, A*) const {
+  template <class TH, class A>
+  __device__ __forceinline__ void site(int i, spinor<TH>& acc, A*) const {
     using T = typename FieldT::T;
-    const spinor<double> mx = m_combine<WField<QCD_PREC_DOUBLE>, false>(x, i, acc, kappa);
-    const spinor<double> bv = b.load(i);
+    const spinor<TH> mx = m_combine<HiT, false>(x, i, acc, (TH)kappa);
+    const spinor<TH> bv = b.load(i);
     spinor<T> sv;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -608,17 +666,17 @@ __global__ void __launch_bounds__(kBlock) w_p_kernel(int V, FieldT r_all, FieldT
 
 // Start-up of one RHS with x = 0: r = rhs (inner precision), p = 0, x_lo = 0, x_hi = 0 and
 // sc->res2 = |rhs|^2 (the residual of the normal equations at x = 0 needs no operator).
-template <class FieldT, class XFieldT>
-__global__ void __launch_bounds__(kBlock) w_start_kernel(int V, WField<QCD_PREC_DOUBLE> rhs, FieldT r, FieldT p,
-                                                         XFieldT x_lo, WField<QCD_PREC_DOUBLE> x_hi, CgScalars* sc,
-                                                         double* partials) {
+template <class HiT, class FieldT, class XFieldT>
+__global__ void __launch_bounds__(kBlock) w_start_kernel(int V, HiT rhs, FieldT r, FieldT p, XFieldT x_lo, HiT x_hi,
+                                                         CgScalars* sc, double* partials) {
   using T = typename FieldT::T;
+  using TH = typename HiT::T;
   double red[1] = {0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
-    const spinor<double> b = rhs.load(i);
+    const spinor<TH> b = rhs.load(i);
     spinor<T> rl, z;
     spinor<typename XFieldT::T> zx;
-    spinor<double> zh;
+    spinor<TH> zh;
     zero(z);
     zero(zx);
     zero(zh);
@@ -630,7 +688,7 @@ __global__ void __launch_bounds__(kBlock) w_start_kernel(int V, WField<QCD_PREC_
     p.store(i, z);
     x_lo.store(i, zx);
     x_hi.store(i, zh);
-    red[0] += norm2(b);
+    accum(red[0], norm2(b));
   }
   double tot[1];
   if (grid_sum_last_block<1>(red, partials, &sc->counter[4], tot) && threadIdx.x == 0) sc->res2 = tot[0];
@@ -668,17 +726,18 @@ __global__ void w_zero_kernel(int V, FieldT f) {
   }
 }
 // x_hi += x_lo, x_lo = 0
-template <class XFieldT>
-__global__ void w_accumulate_kernel(int V, WField<QCD_PREC_DOUBLE> xh, XFieldT xl) {
+template <class HiT, class XFieldT>
+__global__ void w_accumulate_kernel(int V, HiT xh, XFieldT xl) {
+  using TH = typename HiT::T;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
-    spinor<double> a = xh.load(i);
+    spinor<TH> a = xh.load(i);
     const auto b = xl.load(i);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        a.s[q].c[c].re += (double)b.s[q].c[c].re;
-        a.s[q].c[c].im += (double)b.s[q].c[c].im;
+        a.s[q].c[c].re += (TH)b.s[q].c[c].re;
+        a.s[q].c[c].im += (TH)b.s[q].c[c].im;
       }
     xh.store(i, a);
     spinor<typename XFieldT::T> z;
@@ -699,8 +758,15 @@ __global__ void w_pack_links_kernel(Geom g, int V, const double2* __restrict__ c
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
       const double2 d = src[e];
-      if constexpr (PREC == QCD_PREC_DOUBLE) ((double2*)out)[((size_t)mu * 9 + e) * V + i] = make_double2(z * d.x, z * d.y);
-      else ((float2*)out)[((size_t)mu * 9 + e) * V + i] = make_float2((float)(z * d.x), (float)(z * d.y));
+      const size_t o = ((size_t)mu * 9 + e) * V + i;
+      if constexpr (PREC == QCD_PREC_DOUBLE) {
+        ((double2*)out)[o] = make_double2(z * d.x, z * d.y);
+      } else if constexpr (PREC == QCD_PREC_DF64) {
+        const df64 re(z * d.x), im(z * d.y);
+        ((float4*)out)[o] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      } else {
+        ((float2*)out)[o] = make_float2((float)(z * d.x), (float)(z * d.y));
+      }
     }
   }
 }
@@ -710,8 +776,9 @@ __global__ void w_pack_links_kernel(Geom g, int V, const double2* __restrict__ c
 struct WWork {
   CgScalars* sc;           // [R]
   double* partials;        // [max(R, 2)][kMaxPartials]
-  void *b64, *rhs, *x_hi;  // FP64, R fields each: b, M^dagger b, the solution accumulator
-  void* t64;               // FP64 scratch, one field (reliable updates run one RHS at a time)
+  void *b64, *rhs, *x_hi;  // high precision (FP64 or df64, 16 B per complex), R fields each: b,
+                           // M^dagger b, the solution accumulator
+  void* t64;               // high-precision scratch, one field (reliable updates run one RHS at a time)
   void *r, *p, *t;         // inner precision, R fields each
   void* x_lo;              // inner precision, R fields (aliases x_hi in FP64)
   size_t total;
@@ -746,7 +813,9 @@ static WField<PREC> wf(void* p, int V) {
 }
 template <int PREC>
 static WLinks<PREC> wl(const void* p, int V) {
-  return {(const typename std::conditional<PREC == QCD_PREC_DOUBLE, double2, float2>::type*)p, V};
+  using E = typename std::conditional<PREC == QCD_PREC_DOUBLE, double2,
+                                      typename std::conditional<PREC == QCD_PREC_DF64, float4, float2>::type>::type;
+  return {(const E*)p, V};
 }
 
 int launch_wilson_pack_links(const qcd_lattice* lat, const void* canon, void* out, int prec, cudaStream_t st) {
@@ -755,6 +824,7 @@ int launch_wilson_pack_links(const qcd_lattice* lat, const void* canon, void* ou
   const int grid = (int)std::min<long long>((4ll * V + 255) / 256, 152 * 64);
   if (prec == QCD_PREC_DOUBLE) w_pack_links_kernel<QCD_PREC_DOUBLE><<<grid, 256, 0, st>>>(g, V, (const double2*)canon, out);
   else if (prec == QCD_PREC_SINGLE) w_pack_links_kernel<QCD_PREC_SINGLE><<<grid, 256, 0, st>>>(g, V, (const double2*)canon, out);
+  else if (prec == QCD_PREC_DF64) w_pack_links_kernel<QCD_PREC_DF64><<<grid, 256, 0, st>>>(g, V, (const double2*)canon, out);
   else return QCD_ERR_UNSUPPORTED;
   QCD_CUDA(cudaGetLastError());
   return QCD_OK;
@@ -769,6 +839,9 @@ int launch_wilson_pack(const qcd_lattice* lat, void* packed, const void* canon, 
   } else if (prec == QCD_PREC_SINGLE) {
     if (unpack) w_unpack_kernel<<<grid, kBlock, 0, st>>>(V, (double2*)canon, wf<QCD_PREC_SINGLE>(packed, V));
     else w_pack_kernel<<<grid, kBlock, 0, st>>>(V, wf<QCD_PREC_SINGLE>(packed, V), (const double2*)canon);
+  } else if (prec == QCD_PREC_DF64) {
+    if (unpack) w_unpack_kernel<<<grid, kBlock, 0, st>>>(V, (double2*)canon, wf<QCD_PREC_DF64>(packed, V));
+    else w_pack_kernel<<<grid, kBlock, 0, st>>>(V, wf<QCD_PREC_DF64>(packed, V), (const double2*)canon);
   } else {
     return QCD_ERR_UNSUPPORTED;
   }
@@ -796,6 +869,7 @@ static int wilson_op_typed(const qcd_lattice* lat, void* out, const void* in, do
 int launch_wilson_op(const qcd_lattice* lat, void* out, const void* in, double kappa, int mode, int prec, cudaStream_t st) {
   if (prec == QCD_PREC_DOUBLE) return wilson_op_typed<QCD_PREC_DOUBLE>(lat, out, in, kappa, mode, st);
   if (prec == QCD_PREC_SINGLE) return wilson_op_typed<QCD_PREC_SINGLE>(lat, out, in, kappa, mode, st);
+  if (prec == QCD_PREC_DF64) return wilson_op_typed<QCD_PREC_DF64>(lat, out, in, kappa, mode, st);
   return QCD_ERR_UNSUPPORTED;
 }
 
@@ -858,26 +932,29 @@ int launch_wilson_op_mrhs(const qcd_lattice* lat, void* out, const void* in, int
 //   K1  t_r = M p_r, alpha_r = rr_r / |t_r|^2             (multi-RHS operator kernel)
 //   K2  r_r -= alpha_r M^dagger t_r, x_r += alpha_r p_r, beta_r, exit tests
 // A converged or max-iteration RHS drops out of the kernels. Reliable updates (the true residual
-// s = b - M x_hi in FP64, then r_lo = M^dagger s at the inner precision) run per RHS between
-// iterations; a RHS whose residual falls below the tolerance is confirmed by the full FP64 residual
-// of the normal equations, M^dagger b - M^dagger M x_hi, before it stops. The host reads the R
+// s = b - M x_hi at the high precision HI, then r_lo = M^dagger s at the inner precision) run per
+// RHS between iterations; a RHS whose residual falls below the tolerance is confirmed by the full
+// residual of the normal equations at HI, M^dagger b - M^dagger M x_hi, before it stops. HI is FP64,
+// or df64 (opts->prec_outer): the same 16 bytes per complex, a 48-bit significand, and the
+// high-precision operator on the FP32 pipes, which on GB300 run it about five times faster than
+// the FP64 pipe. The host reads the R
 // states after every k iterations (k = opts->check_interval for one RHS, 1 for several, so that a
 // RHS waiting for its update does not idle while the others iterate).
-template <int PREC, int RB>
+template <int PREC, int HI, int RB>
 static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, double kappa, double tol, int max_iter,
                              const qcd_solver_opts& o, void* ws, qcd_solve_info* info, cudaStream_t st) {
   using FT = WField<PREC>;
-  using F64 = WField<QCD_PREC_DOUBLE>;
+  using FH = WField<HI>;  // the high precision: FP64, or df64 on the FP32 pipes
   const Geom g = make_geom(lat);
   const int V = (int)lat->V;
   const bool mixed = PREC != QCD_PREC_DOUBLE;
   WWork w = w_carve(V, PREC, R, (char*)ws);
   auto U = wl<PREC>(lat->wilson_links[PREC], V);
-  auto U64 = wl<QCD_PREC_DOUBLE>(lat->wilson_links[QCD_PREC_DOUBLE], V);
+  auto UH = wl<HI>(lat->wilson_links[HI], V);
   const FT r = wf<PREC>(w.r, V), p = wf<PREC>(w.p, V), t = wf<PREC>(w.t, V), xl = wf<PREC>(w.x_lo, V);
-  const F64 b64 = wf<QCD_PREC_DOUBLE>(w.b64, V), rhs = wf<QCD_PREC_DOUBLE>(w.rhs, V);
-  const F64 xh = wf<QCD_PREC_DOUBLE>(w.x_hi, V), t64 = wf<QCD_PREC_DOUBLE>(w.t64, V);
-  const int grid = one_wave_grid(V, wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true, WEpiResidual<FT, false>>);
+  const FH b64 = wf<HI>(w.b64, V), rhs = wf<HI>(w.rhs, V);
+  const FH xh = wf<HI>(w.x_hi, V), t64 = wf<HI>(w.t64, V);
+  const int grid = one_wave_grid(V, wilson_kernel<WLinks<HI>, FH, true, WEpiResidual<FH, FT, false>>);
   const int grid_ru = one_wave_grid(V, wilson_kernel<WLinks<PREC>, FT, true, WEpiReliableInner<FT>>);
   auto K1 = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RB, WEpiT<FT>>;
   auto K2 = wilson_mrhs_kernel<WLinks<PREC>, FT, true, RB, WEpiUpdate<FT, FT>>;
@@ -905,11 +982,11 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
   };
   int rc = upload();
   if (rc) return rc;
-  // start-up per RHS: rhs_q = M^dagger b_q (FP64); r_q = rhs_q, p_q = x_q = 0; |rhs_q|^2
+  // start-up per RHS: rhs_q = M^dagger b_q (high precision); r_q = rhs_q, p_q = x_q = 0; |rhs_q|^2
   for (int q = 0; q < R; ++q) {
-    if ((rc = launch_wilson_pack(lat, b64.at(q).p, (const char*)b + q * cbytes, QCD_PREC_DOUBLE, false, st))) return rc;
-    wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true><<<grid, kBlock, 0, st>>>(
-        g, V, U64, b64.at(q), WApplyM<F64, true>{b64.at(q), rhs.at(q), kappa});
+    if ((rc = launch_wilson_pack(lat, b64.at(q).p, (const char*)b + q * cbytes, HI, false, st))) return rc;
+    wilson_kernel<WLinks<HI>, FH, true><<<grid, kBlock, 0, st>>>(
+        g, V, UH, b64.at(q), WApplyM<FH, true>{b64.at(q), rhs.at(q), kappa});
     w_start_kernel<<<grid, kBlock, 0, st>>>(V, rhs.at(q), r.at(q), p.at(q), xl.at(q), xh.at(q), w.sc + q, w.partials);
     launches += 3;
   }
@@ -925,29 +1002,29 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
   }
   if ((rc = upload())) return rc;
 
-  // FP64 residual of the normal equations for RHS q: x_hi += x_lo; t64 = M x_hi;
+  // high-precision residual of the normal equations for RHS q: x_hi += x_lo; t64 = M x_hi;
   // res = rhs - M^dagger t64 (-> r_lo unless final_report); sc[q] state from |res|^2
   auto true_residual = [&](int q, bool final_report) -> int {
     if (mixed) w_accumulate_kernel<<<grid, kBlock, 0, st>>>(V, xh.at(q), xl.at(q));
-    wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, false><<<grid, kBlock, 0, st>>>(
-        g, V, U64, xh.at(q), WApplyM<F64, false>{xh.at(q), t64, kappa});
+    wilson_kernel<WLinks<HI>, FH, false><<<grid, kBlock, 0, st>>>(
+        g, V, UH, xh.at(q), WApplyM<FH, false>{xh.at(q), t64, kappa});
     if (final_report)
-      wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true><<<grid, kBlock, 0, st>>>(
-          g, V, U64, t64, WEpiResidual<FT, true>{t64, rhs.at(q), r.at(q), kappa, w.sc + q, w.partials});
+      wilson_kernel<WLinks<HI>, FH, true><<<grid, kBlock, 0, st>>>(
+          g, V, UH, t64, WEpiResidual<FH, FT, true>{t64, rhs.at(q), r.at(q), kappa, w.sc + q, w.partials});
     else
-      wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, true><<<grid, kBlock, 0, st>>>(
-          g, V, U64, t64, WEpiResidual<FT, false>{t64, rhs.at(q), r.at(q), kappa, w.sc + q, w.partials});
+      wilson_kernel<WLinks<HI>, FH, true><<<grid, kBlock, 0, st>>>(
+          g, V, UH, t64, WEpiResidual<FH, FT, false>{t64, rhs.at(q), r.at(q), kappa, w.sc + q, w.partials});
     launches += mixed ? 3 : 2;
     QCD_CUDA(cudaGetLastError());
     return QCD_OK;
   };
 
-  // reliable update of the mixed recursion for RHS q (x_hi += x_lo; s = b - M x_hi in FP64;
+  // reliable update of the mixed recursion for RHS q (x_hi += x_lo; s = b - M x_hi at HI;
   // r_lo = M^dagger s at the inner precision)
   auto reliable_update = [&](int q) -> int {
     w_accumulate_kernel<<<grid, kBlock, 0, st>>>(V, xh.at(q), xl.at(q));
-    wilson_kernel<WLinks<QCD_PREC_DOUBLE>, F64, false><<<grid, kBlock, 0, st>>>(
-        g, V, U64, xh.at(q), WEpiSysResidual<FT>{xh.at(q), b64.at(q), t.at(q), kappa});
+    wilson_kernel<WLinks<HI>, FH, false><<<grid, kBlock, 0, st>>>(
+        g, V, UH, xh.at(q), WEpiSysResidual<FH, FT>{xh.at(q), b64.at(q), t.at(q), kappa});
     wilson_kernel<WLinks<PREC>, FT, true><<<grid_ru, kBlock, 0, st>>>(
         g, V, U, t.at(q), WEpiReliableInner<FT>{t.at(q), r.at(q), kappa, w.sc + q, w.partials});
     launches += 3;
@@ -970,7 +1047,7 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
     bool running = false, updated = false;
     for (int q = 0; q < R; ++q) {
       const int d = h[q].done;
-      if (d == kConverged) {  // confirmed (or refuted) by the full FP64 residual
+      if (d == kConverged) {  // confirmed (or refuted) by the full high-precision residual
         if ((rc = true_residual(q, false))) { cleanup(); return rc; }
         updated = true;
       } else if (mixed && d == kReliable) {
@@ -1006,12 +1083,12 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
     }
   }
   cleanup();
-  // final report: a RHS that ended on a confirmed FP64 residual (kTrueConverged) already holds it
+  // final report: a RHS that ended on a confirmed high-precision residual (kTrueConverged) already holds it
   // in res2 with x_lo folded into x_hi; the others are recomputed here
   for (int q = 0; q < R; ++q)
     if (h[q].done != kTrueConverged && (rc = true_residual(q, true))) return rc;
   for (int q = 0; q < R; ++q)
-    if ((rc = launch_wilson_pack(lat, xh.at(q).p, (char*)x + q * cbytes, QCD_PREC_DOUBLE, true, st))) return rc;
+    if ((rc = launch_wilson_pack(lat, xh.at(q).p, (char*)x + q * cbytes, HI, true, st))) return rc;
   launches += R;
   if ((rc = download())) return rc;
   int status = QCD_OK;
@@ -1047,14 +1124,20 @@ int run_wilson_cgnr(qcd_lattice* lat, int R, void* x, const void* b, double kapp
     set_error("unsupported RHS block %d for Wilson precision %d", o.rhs_block, o.prec_inner);
     return QCD_ERR_INVALID_ARG;
   }
-  if (o.prec_inner == QCD_PREC_DOUBLE) {
-    if (rb == 1) return wilson_cgnr_typed<QCD_PREC_DOUBLE, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
-    return wilson_cgnr_typed<QCD_PREC_DOUBLE, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+  constexpr int D = QCD_PREC_DOUBLE, S = QCD_PREC_SINGLE, DF = QCD_PREC_DF64;
+  if (o.prec_inner == D) {
+    if (rb == 1) return wilson_cgnr_typed<D, D, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+    return wilson_cgnr_typed<D, D, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
   }
-  if (o.prec_inner == QCD_PREC_SINGLE) {
-    if (rb == 1) return wilson_cgnr_typed<QCD_PREC_SINGLE, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
-    if (rb == 2) return wilson_cgnr_typed<QCD_PREC_SINGLE, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
-    return wilson_cgnr_typed<QCD_PREC_SINGLE, 4>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+  if (o.prec_inner == S && o.prec_outer == D) {
+    if (rb == 1) return wilson_cgnr_typed<S, D, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+    if (rb == 2) return wilson_cgnr_typed<S, D, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+    return wilson_cgnr_typed<S, D, 4>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+  }
+  if (o.prec_inner == S && o.prec_outer == DF) {
+    if (rb == 1) return wilson_cgnr_typed<S, DF, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+    if (rb == 2) return wilson_cgnr_typed<S, DF, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
+    return wilson_cgnr_typed<S, DF, 4>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
   }
   return QCD_ERR_UNSUPPORTED;
 }

@@ -51,6 +51,7 @@ class qcd_solver_opts(ctypes.Structure):
         ("block_size", ctypes.c_int),
         ("staged", ctypes.c_int),
         ("wait_cycles", ctypes.c_longlong),
+        ("prec_outer", ctypes.c_int),
     ]
 
 
@@ -107,6 +108,7 @@ SIGNATURES = {
     "qcd_solve_full": (_i, [_vp, _vp, _vp, _d, _d, _i, ctypes.POINTER(qcd_solver_opts), _vp,
                             ctypes.POINTER(qcd_solve_info), _vp]),
     "qcd_fermion_force": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "qcd_device_span_bytes": (_sz, [_vp]),
     "qcd_wilson_field_bytes": (_sz, [_vp, _i]),
     "qcd_wilson_links_bytes": (_sz, [_vp, _i]),
     "qcd_wilson_load_links": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -321,6 +323,10 @@ def qcd_fermion_force(lat, force_dev, links_dev, x_dev, y_dev, stream=None):
 
 
 QCD_WILSON_DSLASH, QCD_WILSON_M, QCD_WILSON_MDAG = 0, 1, 2
+
+
+def qcd_device_span_bytes(ptr) -> int:
+    return _lib.qcd_device_span_bytes(_ptr(ptr))
 
 
 def qcd_wilson_field_bytes(lat, prec) -> int:

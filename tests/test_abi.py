@@ -95,3 +95,38 @@ def test_calls_reject_bad_arguments_before_device_work():
         assert rc == Q.QCD_ERR_NO_LINKS
     finally:
         Q.qcd_lattice_destroy(h)
+
+
+def test_solver_opts_layout_matches_the_library():
+    """The ctypes mirror of qcd_solver_opts covers every field the library writes: the default
+    fill reaches the last field (prec_outer) and nothing past the struct."""
+    import ctypes
+    from paper_1311_2719_gb300 import qcd as Q
+    n = ctypes.sizeof(Q.qcd_solver_opts)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    o = Q.qcd_solver_opts.from_buffer(buf)
+    o.prec_outer = 99
+    Q._lib.qcd_solver_opts_default(ctypes.byref(o))
+    assert o.prec_outer == Q.QCD_PREC_DOUBLE and o.staged == 0 and o.wait_cycles == 0
+    assert bytes(buf[n:]) == b"\xab" * 64
+
+
+def test_wilson_byte_counts():
+    from paper_1311_2719_gb300 import qcd as Q
+    h = Q.qcd_lattice_create(4, 2, 6, 8)
+    try:
+        V = 4 * 2 * 6 * 8
+        assert Q.qcd_wilson_field_bytes(h, Q.QCD_PREC_DOUBLE) == V * 12 * 16
+        assert Q.qcd_wilson_field_bytes(h, Q.QCD_PREC_SINGLE) == V * 12 * 8
+        assert Q.qcd_wilson_field_bytes(h, Q.QCD_PREC_DF64) == V * 12 * 16
+        assert Q.qcd_wilson_field_bytes(h, Q.QCD_PREC_HALF) == 0
+        assert Q.qcd_wilson_links_bytes(h, Q.QCD_PREC_DOUBLE) == V * 4 * 9 * 16
+        assert Q.qcd_wilson_links_bytes(h, Q.QCD_PREC_DF64) == V * 4 * 9 * 16
+        assert Q.qcd_wilson_links_bytes(h, Q.QCD_PREC_SINGLE) == V * 4 * 9 * 8
+        o = Q.qcd_solver_opts_default()
+        o.prec_inner, o.prec_outer = Q.QCD_PREC_SINGLE, Q.QCD_PREC_DF64
+        assert Q.qcd_wilson_workspace_bytes(h, o, 2) > 0
+        o.prec_inner = Q.QCD_PREC_DOUBLE
+        assert Q.qcd_wilson_workspace_bytes(h, o, 2) == 0
+    finally:
+        Q.qcd_lattice_destroy(h)

@@ -9,7 +9,8 @@ from paper_1311_2719_gb300 import qcd as Q
 
 pytestmark = pytest.mark.gpu
 
-TOL = {Q.QCD_PREC_DOUBLE: 1e-12, Q.QCD_PREC_SINGLE: 1e-5}
+TOL = {Q.QCD_PREC_DOUBLE: 1e-12, Q.QCD_PREC_SINGLE: 1e-5, Q.QCD_PREC_DF64: 1e-12}
+ALL = (Q.QCD_PREC_DOUBLE, Q.QCD_PREC_SINGLE, Q.QCD_PREC_DF64)
 
 
 @pytest.fixture(scope="module")
@@ -19,7 +20,7 @@ def H():
 
 
 class WRig:
-    def __init__(self, H, dims, U, precs=(Q.QCD_PREC_DOUBLE, Q.QCD_PREC_SINGLE)):
+    def __init__(self, H, dims, U, precs=ALL):
         import torch
         self.torch, self.H = torch, H
         self.dims = dims
@@ -44,9 +45,10 @@ class WRig:
         Q.qcd_wilson_unpack_field(self.h, out, fout, prec)
         return self.H.host(out)
 
-    def cgnr(self, b, kappa, tol=1e-10, prec=Q.QCD_PREC_DOUBLE, max_iter=10000):
+    def cgnr(self, b, kappa, tol=1e-10, prec=Q.QCD_PREC_DOUBLE, max_iter=10000, outer=Q.QCD_PREC_DOUBLE):
         opts = Q.qcd_solver_opts_default()
         opts.prec_inner = prec
+        opts.prec_outer = outer
         ws = self.lat.empty_bytes(Q.qcd_wilson_workspace_bytes(self.h, opts))
         bd = self.H.dev(b)
         x = self.torch.zeros_like(bd)
@@ -65,7 +67,7 @@ def test_wilson_operators_match_oracle(H, dims):
     kappa = 0.125
     want = {Q.QCD_WILSON_DSLASH: W.dslash_w(U, psi, dims), Q.QCD_WILSON_M: W.apply_m(U, psi, dims, kappa),
             Q.QCD_WILSON_MDAG: W.apply_mdag(U, psi, dims, kappa)}
-    for prec in (Q.QCD_PREC_DOUBLE, Q.QCD_PREC_SINGLE):
+    for prec in ALL:
         for op, w in want.items():
             got = rig.op(psi, kappa, op, prec)
             assert H.rel(got, w) <= TOL[prec], (prec, op, H.rel(got, w))
@@ -92,22 +94,29 @@ def test_wilson_pack_round_trip(H):
     dims = (4, 2, 6, 2)
     psi = I.make_spinor(dims, seed=8)
     rig = WRig(H, dims, I.make_links(dims, "unit"), precs=(Q.QCD_PREC_DOUBLE,))
-    for prec in (Q.QCD_PREC_DOUBLE, Q.QCD_PREC_SINGLE):
+    def df64_round(v):  # hi = nearest float, lo = nearest float to the (exact) remainder
+        hi = v.astype(np.float32).astype(np.float64)
+        return hi + (v - hi).astype(np.float32).astype(np.float64)
+
+    for prec in ALL:
         f = rig.field(prec)
         Q.qcd_wilson_pack_field(rig.h, f, H.dev(psi), prec)
         back = torch.zeros((rig.V, 4, 3), dtype=torch.complex128, device="cuda")
         Q.qcd_wilson_unpack_field(rig.h, back, f, prec)
-        want = psi if prec == Q.QCD_PREC_DOUBLE else psi.astype(np.complex64).astype(np.complex128)
+        want = {Q.QCD_PREC_DOUBLE: psi, Q.QCD_PREC_SINGLE: psi.astype(np.complex64).astype(np.complex128),
+                Q.QCD_PREC_DF64: df64_round(psi.real) + 1j * df64_round(psi.imag)}[prec]
         assert np.array_equal(H.host(back), want)
+    assert np.max(np.abs(want - psi) / np.abs(psi)) <= 2.0 ** -47
 
 
-@pytest.mark.parametrize("prec", [Q.QCD_PREC_DOUBLE, Q.QCD_PREC_SINGLE])
+@pytest.mark.parametrize("prec,outer", [(Q.QCD_PREC_DOUBLE, Q.QCD_PREC_DOUBLE), (Q.QCD_PREC_SINGLE, Q.QCD_PREC_DOUBLE),
+                                        (Q.QCD_PREC_SINGLE, Q.QCD_PREC_DF64)])
 @pytest.mark.parametrize("dims,kappa", [((4, 4, 4, 4), 0.125), ((2, 4, 6, 8), 0.14), ((6, 6, 4, 4), 0.1)])
-def test_wilson_cgnr_matches_oracle(H, prec, dims, kappa):
+def test_wilson_cgnr_matches_oracle(H, prec, outer, dims, kappa):
     U = I.make_links(dims, kind="haar", seed=1)
     b = I.make_spinor(dims, seed=2)
     rig = WRig(H, dims, U)
-    rc, info, x = rig.cgnr(b, kappa, 1e-10, prec)
+    rc, info, x = rig.cgnr(b, kappa, 1e-10, prec, outer=outer)
     assert rc == Q.QCD_OK, info
     assert info["true_rel_residual"] <= 1e-10
     rhs = W.apply_mdag(U, b, dims, kappa)
@@ -144,11 +153,15 @@ def test_wilson_full_size_32c64(H):
     V = S.volume(dims)
     rng = np.random.default_rng(3)
     sites = np.unique(np.concatenate([rng.choice(V, 1500, replace=False), [0, V - 1, V // 2]]))
-    for prec in (Q.QCD_PREC_DOUBLE, Q.QCD_PREC_SINGLE):
+    for prec in ALL:
         got = rig.op(b, kappa, Q.QCD_WILSON_DSLASH, prec)
         assert H.rel(got[sites], W.dslash_w_sites(U, b, dims, sites)) <= TOL[prec]
     rc, info, x = rig.cgnr(b, kappa, 1e-10, Q.QCD_PREC_SINGLE)
     assert rc == Q.QCD_OK and info["true_rel_residual"] <= 1e-10
+    rc, info_df, x_df = rig.cgnr(b, kappa, 1e-10, Q.QCD_PREC_SINGLE, outer=Q.QCD_PREC_DF64)
+    assert rc == Q.QCD_OK and info_df["true_rel_residual"] <= 1e-10
+    assert info_df["iterations"] == info["iterations"]
+    assert H.rel(x_df, x) <= 1e-8
 
 
 # ---------------------------------------------------------------- several right-hand sides
@@ -190,11 +203,13 @@ def test_wilson_op_mrhs_matches_oracle(H, dims, nrhs):
                 assert H.rel(got[k], f(psis[k])) <= TOL[prec], (prec, op, k)
 
 
-def _cgnr_mrhs(rig, bs, kappa, tol=1e-10, prec=Q.QCD_PREC_SINGLE, rhs_block=0, max_iter=10000):
+def _cgnr_mrhs(rig, bs, kappa, tol=1e-10, prec=Q.QCD_PREC_SINGLE, rhs_block=0, max_iter=10000,
+               outer=Q.QCD_PREC_DOUBLE):
     torch = rig.torch
     n = len(bs)
     opts = Q.qcd_solver_opts_default()
     opts.prec_inner = prec
+    opts.prec_outer = outer
     opts.rhs_block = rhs_block
     ws = rig.lat.empty_bytes(Q.qcd_wilson_workspace_bytes(rig.h, opts, n))
     bd = rig.H.dev(np.stack(bs))
@@ -206,14 +221,17 @@ def _cgnr_mrhs(rig, bs, kappa, tol=1e-10, prec=Q.QCD_PREC_SINGLE, rhs_block=0, m
     return rc, infos, rig.H.host(x)
 
 
-@pytest.mark.parametrize("prec,rhs_block", [(Q.QCD_PREC_SINGLE, 0), (Q.QCD_PREC_SINGLE, 1), (Q.QCD_PREC_SINGLE, 2),
-                                            (Q.QCD_PREC_SINGLE, 4), (Q.QCD_PREC_DOUBLE, 0), (Q.QCD_PREC_DOUBLE, 2)])
-def test_wilson_cgnr_mrhs_matches_oracle(H, prec, rhs_block):
+@pytest.mark.parametrize("prec,rhs_block,outer", [
+    (Q.QCD_PREC_SINGLE, 0, Q.QCD_PREC_DOUBLE), (Q.QCD_PREC_SINGLE, 1, Q.QCD_PREC_DOUBLE),
+    (Q.QCD_PREC_SINGLE, 2, Q.QCD_PREC_DOUBLE), (Q.QCD_PREC_SINGLE, 4, Q.QCD_PREC_DOUBLE),
+    (Q.QCD_PREC_DOUBLE, 0, Q.QCD_PREC_DOUBLE), (Q.QCD_PREC_DOUBLE, 2, Q.QCD_PREC_DOUBLE),
+    (Q.QCD_PREC_SINGLE, 0, Q.QCD_PREC_DF64), (Q.QCD_PREC_SINGLE, 2, Q.QCD_PREC_DF64)])
+def test_wilson_cgnr_mrhs_matches_oracle(H, prec, rhs_block, outer):
     dims, kappa = (4, 4, 4, 4), 0.125
     U = I.make_links(dims, kind="haar", seed=1)
     bs = list(_spinors(dims, 5))
     rig = WRig(H, dims, U)
-    rc, infos, x = _cgnr_mrhs(rig, bs, kappa, 1e-10, prec, rhs_block)
+    rc, infos, x = _cgnr_mrhs(rig, bs, kappa, 1e-10, prec, rhs_block, outer=outer)
     assert rc == Q.QCD_OK, infos
     for k, b in enumerate(bs):
         assert infos[k]["converged"] and infos[k]["true_rel_residual"] <= 1e-10
@@ -265,6 +283,70 @@ def test_wilson_mrhs_argument_checks(H):
         assert rc == Q.QCD_ERR_INVALID_ARG
     rc, _ = Q.qcd_wilson_cgnr_mrhs(rig.h, 0, x, bd, 0.1, 1e-10, 100, None, ws, raise_on=())
     assert rc == Q.QCD_ERR_INVALID_ARG
+
+
+def test_wilson_df64_outer_argument_checks(H):
+    """df64 is an outer precision of the mixed CGNR only, needs its own links, and is not a
+    multi-RHS operator precision."""
+    dims = (2, 2, 2, 2)
+    U = I.make_links(dims, kind="haar", seed=1)
+    rig = WRig(H, dims, U, precs=(Q.QCD_PREC_DOUBLE, Q.QCD_PREC_SINGLE))
+    b = I.make_spinor(dims, seed=2)
+    bd = H.dev(b)
+    x = rig.torch.zeros_like(bd)
+    ws = rig.lat.empty_bytes(Q.qcd_wilson_workspace_bytes(rig.h, Q.qcd_solver_opts_default(), 1))
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner, opts.prec_outer = Q.QCD_PREC_DOUBLE, Q.QCD_PREC_DF64
+    assert Q.qcd_wilson_workspace_bytes(rig.h, opts, 1) == 0
+    rc, _ = Q.qcd_wilson_cgnr(rig.h, x, bd, 0.1, 1e-10, 100, opts, ws, raise_on=())
+    assert rc == Q.QCD_ERR_INVALID_ARG
+    opts.prec_inner = Q.QCD_PREC_SINGLE
+    o64 = Q.qcd_solver_opts_default()
+    o64.prec_inner = Q.QCD_PREC_SINGLE
+    assert Q.qcd_wilson_workspace_bytes(rig.h, opts, 1) == Q.qcd_wilson_workspace_bytes(rig.h, o64, 1) > 0
+    rc, _ = Q.qcd_wilson_cgnr(rig.h, x, bd, 0.1, 1e-10, 100, opts, ws, raise_on=())
+    assert rc == Q.QCD_ERR_NO_LINKS
+    fb = Q.qcd_wilson_field_bytes(rig.h, Q.QCD_PREC_DF64)
+    assert fb == Q.qcd_wilson_field_bytes(rig.h, Q.QCD_PREC_DOUBLE)
+    f_in, f_out = rig.lat.empty_bytes(fb), rig.lat.empty_bytes(fb)
+    with pytest.raises(Q.QcdError) as e:
+        Q.qcd_wilson_op_mrhs(rig.h, f_out, f_in, 1, 0.1, Q.QCD_WILSON_M, Q.QCD_PREC_DF64)
+    assert e.value.status == Q.QCD_ERR_INVALID_ARG
+    with pytest.raises(Q.QcdError) as e:
+        Q.qcd_wilson_op(rig.h, f_out, f_in, 0.1, Q.QCD_WILSON_M, Q.QCD_PREC_DF64)
+    assert e.value.status == Q.QCD_ERR_NO_LINKS
+
+
+def test_short_buffers_are_rejected_before_device_work(H):
+    """A workspace or field shorter than the call needs is refused with QCD_ERR_INVALID_ARG. Each
+    short buffer is a view near the end of one cudaMalloc'd block; the call is made only when the
+    library's own span query shows the buffer short, so the argument check alone decides it."""
+    import torch
+    dims = (8, 8, 8, 8)
+    U = I.make_links(dims, kind="haar", seed=1)
+    rig = WRig(H, dims, U)
+    b = H.dev(I.make_spinor(dims, seed=2))
+    x = torch.zeros_like(b)
+    opts = Q.qcd_solver_opts_default()
+    opts.prec_inner = Q.QCD_PREC_SINGLE
+    need = Q.qcd_wilson_workspace_bytes(rig.h, opts, 1)
+    block = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    short = block[(64 << 20) - (need // 2 // 256) * 256:]
+    span = Q.qcd_device_span_bytes(short)
+    if span == 0 or span >= need:
+        pytest.skip(f"allocation span not measurable here ({span} bytes)")
+    assert Q.qcd_device_span_bytes(block) >= 64 << 20
+    rc, info = Q.qcd_wilson_cgnr(rig.h, x, b, 0.12, 1e-10, 100, opts, short, raise_on=())
+    assert rc == Q.QCD_ERR_INVALID_ARG and info["iterations"] == 0
+    assert "workspace_dev" in Q._lib.qcd_last_error().decode()
+    fb = Q.qcd_wilson_field_bytes(rig.h, Q.QCD_PREC_SINGLE)
+    fout = block[(64 << 20) - (fb // 2 // 256) * 256:]
+    assert 0 < Q.qcd_device_span_bytes(fout) < fb
+    fin = rig.field(Q.QCD_PREC_SINGLE)
+    with pytest.raises(Q.QcdError) as e:
+        Q.qcd_wilson_op(rig.h, fout, fin, 0.12, Q.QCD_WILSON_M, Q.QCD_PREC_SINGLE)
+    assert e.value.status == Q.QCD_ERR_INVALID_ARG
+    torch.cuda.synchronize()
 
 
 def test_wilson_full_size_32c64_8rhs(H):
