@@ -70,13 +70,16 @@ WORKLOADS = {
                                desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion with "
                                     "FP64 reliable updates, to 1e-10"),
     "wilson32c64_single_df64": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
-                                    inner="single18", nrhs=1, outer="df64", traffic_key="wilson32c64_single",
+                                    inner="single18", nrhs=1, outer="df64", reliable_delta=0.01,
+                                    traffic_key="wilson32c64_single",
                                     desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, CGNR on M^dagger M: FP32 recursion "
-                                         "with df64 reliable updates and solution, to 1e-10"),
+                                         "with df64 reliable updates (delta 0.01) and solution, to 1e-10"),
     "wilson32c64_8rhs_df64": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
-                                  inner="single18", nrhs=8, outer="df64", traffic_key="wilson32c64_8rhs",
+                                  inner="single18", nrhs=8, outer="df64", reliable_delta=0.01,
+                                  traffic_key="wilson32c64_8rhs",
                                   desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, 8 RHS in one multi-RHS CGNR on "
-                                       "M^dagger M: FP32 recursion with df64 reliable updates and solution, to 1e-10"),
+                                       "M^dagger M: FP32 recursion with df64 reliable updates (delta 0.01) and "
+                                       "solution, to 1e-10"),
     "full32_single12": dict(kind_solve="full", dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="single12",
                             desc="full-system solve M x = b (both parities) on 32^4 Haar, m=0.01: even-odd reduction "
                                  "onto the mixed CG (FP32 recon-12 inner, FP64 reliable updates), full FP64 residual 1e-10"),
@@ -617,6 +620,9 @@ def run_gpu_wilson(args, wl):
     bufs = {p: lat.empty_bytes(Q.qcd_wilson_links_bytes(lat.handle, p)) for p in (0, 1, 3)}
     opts = Q.qcd_solver_opts_default()
     opts.prec_inner, opts.prec_outer = 1, outer
+    delta = args.reliable_delta if args.reliable_delta is not None else wl.get("reliable_delta")
+    if delta is not None:
+        opts.reliable_delta = delta
     ws = {1: lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))}  # FP32 inner, either outer
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     launches_links = 2
@@ -748,7 +754,7 @@ def run_gpu_wilson(args, wl):
         "config": {"workload": wl["desc"], "dims": list(dims), "kappa": kappa, "tol": tol, "nrhs": R,
                    "parallelism": f"replicas x{world} (no sharding)",
                    "l2": "flushed before every step (512 MB write, outside the timed events)",
-                   "outer": wl.get("outer", "double"),
+                   "outer": wl.get("outer", "double"), "reliable_delta": opts.reliable_delta,
                    "step": "qcd_wilson_load_links (" + ("FP64" if outer == 0 else "df64") +
                            " + FP32) + qcd_wilson_cgnr_mrhs"},
         "cg": {"iterations": [i["iterations"] for i in runs[-1]],
@@ -1196,6 +1202,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune", action="store_true", help="run the autotuner before the batched workloads")
     ap.add_argument("--no-variant", action="store_true", help="skip the df64 run beside an FP64 workload")
+    ap.add_argument("--reliable-delta", type=float, default=None,
+                    help="mixed Wilson CGNR: reliable-update threshold (default: the workload's, else the library's)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
