@@ -332,5 +332,11 @@ def solve_full(U, b, dims, mass: float, tol: float, max_iter: int, tbc: float = 
         p = r + (rr_new / rr) * p
         rr = rr_new
         it += 1
+    return {"x": x, "iterations": it, "rel_residual": full_residual(U, x, b, dims, mass, tbc)}
+
+
+def full_residual(U, x, b, dims, mass: float, tbc: float = -1.0) -> float:
+    """|b - M x| / |b| in FP64 over both parities, M = m + D."""
+    b = np.asarray(b, np.complex128)
     res = b - apply_m(U, x, dims, mass, tbc)
-    return {"x": x, "iterations": it, "rel_residual": float(np.sqrt(_norm2(res) / _norm2(b)))}
+    return float(np.sqrt(_norm2(res) / _norm2(b)))

@@ -93,10 +93,19 @@ def cgnr(U, b, dims, kappa: float, tol: float, max_iter: int, tbc: float = -1.0)
         p = r + (rr_new / rr) * p
         rr = rr_new
         it += 1
+    out = {"x": x, "iterations": it, "converged": rr < stop}
+    out.update(residuals(U, x, b, dims, kappa, tbc))
+    return out
+
+
+def residuals(U, x, b, dims, kappa: float, tbc: float = -1.0) -> dict:
+    """The two FP64 residuals of a solution x of M x = b: rel_residual = |b - M x| / |b| and
+    normal_rel_residual = |M^dagger b - M^dagger M x| / |M^dagger b| (the CGNR's own system)."""
+    b = np.asarray(b, np.complex128)
+    rhs = apply_mdag(U, b, dims, kappa, tbc)
     nres = rhs - apply_mdag(U, apply_m(U, x, dims, kappa, tbc), dims, kappa, tbc)
     res = b - apply_m(U, x, dims, kappa, tbc)
-    return {"x": x, "iterations": it, "converged": rr < stop,
-            "normal_rel_residual": float(np.sqrt(_n2(nres) / _n2(rhs))),
+    return {"normal_rel_residual": float(np.sqrt(_n2(nres) / _n2(rhs))),
             "rel_residual": float(np.sqrt(_n2(res) / _n2(b)))}
 
 

@@ -318,3 +318,92 @@ def test_full_system_solve_matches_dense(dims):
     res = S.solve_full(U, b, dims, m, tol=1e-13, max_iter=5000)
     assert res["rel_residual"] <= 1e-11
     assert _rel(res["x"], x_dense) <= 1e-10
+
+
+# ---------------------------------------------------------------- residual checkers (exact values)
+#
+# Every GPU solve test recomputes the residual of the GPU's solution with the oracle's checkers, so
+# the checkers are pinned to exact values: with x_exact from a dense LAPACK solve, the scaled
+# x = (1 - eps) x_exact leaves the residual b - A x = eps b, i.e. a relative residual of eps
+# exactly, for any eps (up to the O(1e-15) rounding of the dense solve). A missing square root
+# (eps^2), a missing or wrong normalisation (eps |b|, eps |b_e| / |b|) or a residual that ignores
+# x fails it.
+
+RES_EPS = (0.3, 1e-4, 1e-8)
+
+
+def _dense_even_solution(U, b, dims, m):
+    """x_e = A^-1 b_e by LAPACK on the dense even-site A; full-lattice vector, odd half 0."""
+    ev_idx = np.nonzero(S.parity(dims) == 0)[0]
+    V = S.volume(dims)
+
+    def apply_a(v_even):
+        full = np.zeros((V, 3), np.complex128)
+        full[ev_idx] = v_even
+        return S.mdagm(U, full, dims, m)[ev_idx]
+
+    A = S.dense_operator(apply_a, len(ev_idx))
+    x = np.zeros((V, 3), np.complex128)
+    x[ev_idx] = np.linalg.solve(A, b[ev_idx].reshape(-1)).reshape(-1, 3)
+    return x
+
+
+def _dense_full_solution(U, b, dims, m):
+    """x = M^-1 b on both parities (M = m + D) by LAPACK on the dense M."""
+    M = S.dense_operator(lambda v: S.apply_m(U, v, dims, m), S.volume(dims))
+    return np.linalg.solve(M, b.reshape(-1)).reshape(-1, 3)
+
+
+def _residual_pins(dims):
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)  # odd half non-zero: the even checker must ignore it
+    m = 0.5
+    xe = _dense_even_solution(U, b, dims, m)
+    xf = _dense_full_solution(U, b, dims, m)
+    for eps in RES_EPS:
+        got = S.true_residual(U, (1.0 - eps) * xe, b, dims, m)
+        assert abs(got - eps) <= 1e-13, ("true_residual", eps, got)
+        got = S.full_residual(U, (1.0 - eps) * xf, b, dims, m)
+        assert abs(got - eps) <= 1e-13, ("full_residual", eps, got)
+
+
+def _residual_pins_pass():
+    try:
+        for dims in ((2, 2, 2, 2), (2, 4, 6, 8)):
+            _residual_pins(dims)
+    except AssertionError:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 6, 8)])
+def test_residual_checkers_are_exact_on_scaled_dense_solutions(dims):
+    _residual_pins(dims)
+
+
+@pytest.mark.parametrize("mistake", ["no_sqrt", "unnormalised", "full_b_norm", "ignores_x_sign"])
+def test_planted_residual_mistake_fails_its_pin(monkeypatch, mistake):
+    """Plant a plausible mistake in the oracle's residual checkers (on the CPU): the exact-value pin
+    must catch it."""
+    def norm2(a):
+        return float(np.vdot(a.reshape(-1), a.reshape(-1)).real)
+
+    def even(dims, v):
+        return np.where((S.parity(dims) == 0)[:, None], v, 0.0)
+
+    def wrong_true(U, x, b, dims, mass, tbc=-1.0):
+        be = even(dims, b)
+        if mistake == "ignores_x_sign":
+            res = be + S.mdagm(U, x, dims, mass, tbc)
+        else:
+            res = be - S.mdagm(U, x, dims, mass, tbc)
+        if mistake == "no_sqrt":
+            return norm2(res) / norm2(be)
+        if mistake == "unnormalised":
+            return float(np.sqrt(norm2(res)))
+        if mistake == "full_b_norm":
+            return float(np.sqrt(norm2(res) / norm2(b)))
+        return float(np.sqrt(norm2(res) / norm2(be)))
+
+    monkeypatch.setattr(S, "true_residual", wrong_true)
+    assert not _residual_pins_pass()

@@ -128,3 +128,52 @@ def test_planted_mistake_in_wilson_oracle_fails_a_pin(monkeypatch, mistake):
         except AssertionError:
             failed = True
     assert failed
+
+
+# ---------------------------------------------------------------- residual checkers (exact values)
+#
+# x = (1 - eps) M^-1 b (dense LAPACK) leaves b - M x = eps b and M^dagger b - M^dagger M x =
+# eps M^dagger b: both relative residuals equal eps exactly, for any eps.
+
+
+def _wilson_residual_pins(dims):
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = _spinor(dims, 2)
+    kappa = 0.12
+    n = S.volume(dims) * 12
+    cols = []
+    for j in range(n):
+        e = np.zeros(n, np.complex128)
+        e[j] = 1.0
+        cols.append(W.apply_m(U, e.reshape(-1, 4, 3), dims, kappa).reshape(-1))
+    x_exact = np.linalg.solve(np.stack(cols, axis=1), b.reshape(-1)).reshape(-1, 4, 3)
+    for eps in (0.3, 1e-4, 1e-8):
+        r = W.residuals(U, (1.0 - eps) * x_exact, b, dims, kappa)
+        assert abs(r["rel_residual"] - eps) <= 1e-13, (eps, r)
+        assert abs(r["normal_rel_residual"] - eps) <= 1e-13, (eps, r)
+
+
+def test_wilson_residual_checkers_are_exact():
+    _wilson_residual_pins((2, 2, 2, 2))
+
+
+@pytest.mark.parametrize("mistake", ["no_sqrt", "unnormalised", "normal_wrong_norm"])
+def test_planted_wilson_residual_mistake_fails_its_pin(monkeypatch, mistake):
+    orig = W.residuals
+
+    def wrong(U, x, b, dims, kappa, tbc=-1.0):
+        r = orig(U, x, b, dims, kappa, tbc)
+        if mistake == "no_sqrt":
+            r = {k: v * v for k, v in r.items()}
+        elif mistake == "unnormalised":
+            r["rel_residual"] *= float(np.linalg.norm(b))
+        else:
+            # the normal residual normalised by |b| instead of |M^dagger b|
+            rhs = W.apply_mdag(U, b, dims, kappa, tbc)
+            nres = rhs - W.apply_mdag(U, W.apply_m(U, x, dims, kappa, tbc), dims, kappa, tbc)
+            r["normal_rel_residual"] = float(np.linalg.norm(nres) / np.linalg.norm(b))
+        return r
+
+    monkeypatch.setattr(W, "residuals", wrong)
+    with pytest.raises(AssertionError):
+        _wilson_residual_pins((2, 2, 2, 2))
