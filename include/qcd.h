@@ -198,10 +198,13 @@ QCD_API int qcd_mdagm(const qcd_lattice* lat, void* out_dev, const void* in_dev,
  * possible or not permitted. Here the intermediate odd-parity field lives in a 16 MiB array inside
  * the library (a file-scope __device__ array that every GPU loading the library keeps until the
  * process exits); the caller passes only `in_dev` and `out_dev`, and nothing is allocated.
- *   Limit: qcd_field_bytes(lat, prec) must be <= 16 MiB (e.g. FP64 up to V/2 = 349525 sites,
- *   24^4; FP32 and FP16 up to 32^4); larger lattices get QCD_ERR_INVALID_ARG.
+ *   Limit: qcd_field_bytes(lat, prec) must be <= 16 MiB (e.g. FP64 and DF64 up to V/2 = 349525
+ *   sites, 24^4; FP32 and FP16 up to 32^4); larger lattices get QCD_ERR_INVALID_ARG.
+ *   The lattice's device (qcd_lattice_device) must be the current device, else
+ *   QCD_ERR_INVALID_ARG: the array used is the current device's copy.
  *   The first call on each device looks up the array's device address with that device current;
- *   make that first call before any stream capture.
+ *   make that first call before any stream capture. The address is looked up again when the
+ *   device's context has changed since (after a device reset, for instance).
  *   All calls share the one array and it keeps the last call's contents (the operator overwrites
  *   it completely before reading it). Calls whose executions overlap on the GPU — e.g. on two
  *   streams at once — race on it; serialise them. */

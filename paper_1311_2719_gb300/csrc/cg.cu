@@ -156,7 +156,9 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
   if ((rc = read_scalars(R.w, &h, st))) return rc;
   const double true_rel = h.bb > 0 ? std::sqrt(h.res2 / h.bb) : 0.0;
   if (h.fault) {
-    set_error("a bounded device-side wait in the staged operator gave up");
+    set_error(h.fault == 1 ? "a bounded device-side wait in the staged operator gave up"
+                           : "a bounded device-side wait in the staged operator gave up, and so did the wait for "
+                             "its bulk copies in flight (the launch's outputs are undefined)");
     status = QCD_ERR_TIMEOUT;
   } else if (status == QCD_OK && !(true_rel <= tol)) {
     // The recursion met the tolerance but the FP64 residual did not (possible in plain FP64 CG

@@ -14,7 +14,8 @@ namespace qcd {
 struct __align__(256) CgScalars {
   double rr, rr_prev, pp, alpha, beta, delit, bb, m2, res2, rmax2, delta2, tol2;
   int iter, max_iter, done, since_ru, ru_count, ru_interval, mixed, loops;
-  int fault;  // set by a kernel whose bounded device-side wait gave up
+  int fault;  // set by a kernel whose bounded device-side wait gave up: 1, or 2 when its drain of the
+              // copies in flight gave up as well
   unsigned counter[16];
 };
 static_assert(sizeof(CgScalars) <= 256, "scalars block");

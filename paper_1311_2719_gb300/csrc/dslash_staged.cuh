@@ -14,8 +14,9 @@
 // of the index range) is read from global memory instead. Bulk copies need 16-byte aligned sources
 // and sizes: the 8-byte vector planes are staged from an even index to an even index.
 //
-// Every wait on an mbarrier is bounded (clock64); on expiry the kernel records a fault in the CG
-// scalars, waits (bounded again) for the copies it issued, and returns.
+// Every wait on an mbarrier is bounded (clock64); on expiry the kernel waits (bounded again) for the
+// copies it issued, records a fault in the CG scalars (2 when that drain gave up as well), and
+// returns. Once a fault is set the launch's outputs are undefined.
 //
 // Measured on GB300 (32^4, FP32 recon-12): 123 us per operator launch against 52 us for the
 // direct-load kernel. Each site needs ~600 staged bytes (every neighbour vector is staged once per
@@ -253,11 +254,15 @@ __global__ void __launch_bounds__(kStageSites) dslash_staged_fp32r12_kernel(Geom
     __syncthreads();  // stage sidx is refilled by the next iteration's copies
   }
   if (!ok) {
-    if (fault && threadIdx.x == 0) atomicExch(fault, 1);
     // let the copies this block issued land before its shared memory is released (bounded again, by
     // the default limit whatever the caller's)
+    bool drained = true;
     for (int q = 0; q < 2; ++q)
-      if (in_flight[q]) mbar_wait_bounded(&bar[q], phase[q], kWaitCycles);
+      if (in_flight[q] && !mbar_wait_bounded(&bar[q], phase[q], kWaitCycles)) drained = false;
+    // 1: a wait gave up and the block's copies landed; 2: the drain gave up too, so copies may still
+    // be landing in shared memory that a later block of this launch owns. Either way the launch's
+    // outputs are undefined and the solve stops with QCD_ERR_TIMEOUT.
+    if (fault && threadIdx.x == 0) atomicMax(fault, drained ? 1 : 2);
     return;
   }
   if constexpr (Epi::NV > 0) epi.finish(red);

@@ -26,23 +26,51 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_mdagm_scratch[kNoAllocScratchBytes];
 
 static std::mutex g_scratch_mutex;
-static void* g_scratch_ptr[kMaxDevices] = {};
+// Per device: the context the address was looked up in, and the address. A device reset gives the
+// device a new primary context in which the module (and the array) is loaded afresh, so the
+// address is looked up again whenever the current context differs from the cached one.
+struct ScratchSlot {
+  void* ctx = nullptr;
+  void* ptr = nullptr;
+};
+static ScratchSlot g_scratch_slot[kMaxDevices];
 
-// Device address of g_mdagm_scratch on `dev` (the current device). First use per device does the
-// lookup; later calls read the cached pointer.
+// The current context (the driver's cuCtxGetCurrent, fetched at run time), or nullptr when the
+// driver does not provide it.
+static void* current_context() {
+  using GetCurrent = int (*)(void**);
+  static const GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    cudaGetLastError();
+    return (GetCurrent)f;
+  }();
+  void* ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
+
+// Device address of g_mdagm_scratch on `dev` (the current device). The first use per device and
+// context does the lookup; later calls read the cached pointer.
 static int scratch_for_device(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("device ordinal %d outside the supported range [0, %d)", dev, kMaxDevices);
     return QCD_ERR_UNSUPPORTED;
   }
+  void* ctx = current_context();
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
+  ScratchSlot& slot = g_scratch_slot[dev];
+  if (!slot.ptr || slot.ctx != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_mdagm_scratch);
     if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
-    g_scratch_ptr[dev] = p;
+    slot.ptr = p;
+    slot.ctx = ctx;
   }
-  *out = g_scratch_ptr[dev];
+  *out = slot.ptr;
   return QCD_OK;
 }
 
@@ -59,7 +87,7 @@ extern "C" int qcd_mdagm_noalloc(const qcd_lattice* lat, void* out_dev, const vo
     return QCD_ERR_INVALID_ARG;
   }
   if (out_dev == in_dev) { set_error("out_dev must not alias in_dev"); return QCD_ERR_INVALID_ARG; }
-  if (prec != QCD_PREC_DOUBLE && prec != QCD_PREC_SINGLE && prec != QCD_PREC_HALF) {
+  if (prec != QCD_PREC_DOUBLE && prec != QCD_PREC_SINGLE && prec != QCD_PREC_HALF && prec != QCD_PREC_DF64) {
     set_error("unknown precision %d", prec);
     return QCD_ERR_INVALID_ARG;
   }
@@ -85,6 +113,12 @@ extern "C" int qcd_mdagm_noalloc(const qcd_lattice* lat, void* out_dev, const vo
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  // The kernels run on the current device and the scratch is that device's copy of the array, so
+  // the lattice's links must live there too.
+  if (lat->device != dev) {
+    set_error("the lattice belongs to device %d, current device is %d", lat->device, dev);
+    return QCD_ERR_INVALID_ARG;
+  }
   void* scratch = nullptr;
   if (int rc = scratch_for_device(dev, &scratch)) return rc;
   // The scratch is overwritten at every site by the first half-lattice hop before it is read,

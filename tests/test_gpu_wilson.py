@@ -143,6 +143,28 @@ def test_wilson_status_codes(H):
     assert rc == Q.QCD_OK and not np.any(x)
 
 
+def _sampled_normal_residual(U, x, b, dims, kappa, sites):
+    """|M^dagger b - M^dagger M x| / |M^dagger b| restricted to `sites`, by the oracle's site-local
+    operator: b - M x is formed on the sites next to the samples, then M^dagger of it at the samples."""
+    L = list(dims)
+    stride = [1, L[0], L[0] * L[1], L[0] * L[1] * L[2]]
+    near = set()
+    for s_ in sites:
+        c = [(s_ // stride[m]) % L[m] for m in range(4)]
+        near.add(int(s_))
+        for m in range(4):
+            for d in (1, -1):
+                near.add(int(s_ + (((c[m] + d) % L[m]) - c[m]) * stride[m]))
+    near = np.array(sorted(near))
+    res = np.zeros_like(b)  # b - M x on the sites next to the samples
+    res[near] = b[near] - (x[near] - kappa * W.dslash_w_sites(U, x, dims, near))
+    g5r = W.gamma5(res)
+    nres = W.gamma5(g5r[sites] - kappa * W.dslash_w_sites(U, g5r, dims, sites))  # M^dagger (b - M x)
+    g5b = W.gamma5(b)
+    rhs = W.gamma5(g5b[sites] - kappa * W.dslash_w_sites(U, g5b, dims, sites))
+    return float(np.linalg.norm(nres) / np.linalg.norm(rhs))
+
+
 def test_wilson_full_size_32c64(H):
     """32^3 x 64, kappa = 0.125, Haar links: sampled-site operator parity and a mixed CGNR to 1e-10."""
     dims = (32, 32, 32, 64)
@@ -162,6 +184,10 @@ def test_wilson_full_size_32c64(H):
     assert rc == Q.QCD_OK and info_df["true_rel_residual"] <= 1e-10
     assert info_df["iterations"] == info["iterations"]
     assert H.rel(x_df, x) <= 1e-8
+    # oracle: the normal-equation residual of both solutions recomputed at sampled sites
+    sites = np.random.default_rng(7).choice(V, 64, replace=False)
+    for sol in (x, x_df):
+        assert _sampled_normal_residual(U, sol, b, dims, kappa, sites) <= 1e-9
 
 
 # ---------------------------------------------------------------- several right-hand sides
@@ -368,25 +394,8 @@ def test_wilson_full_size_32c64_8rhs(H):
     assert rc1 == Q.QCD_OK
     assert H.rel(x[0], x1) <= 1e-8
     # oracle: (M^dagger b - M^dagger M x) at sampled sites, relative to |M^dagger b| there
-    V = S.volume(dims)
     rng = np.random.default_rng(7)
-    sites = rng.choice(V, 64, replace=False)
-    L = list(dims)
-    stride = [1, L[0], L[0] * L[1], L[0] * L[1] * L[2]]
+    sites = rng.choice(S.volume(dims), 64, replace=False)
     for k in (0, 7):
-        near = set()
-        for s_ in sites:
-            c = [(s_ // stride[m]) % L[m] for m in range(4)]
-            near.add(int(s_))
-            for m in range(4):
-                for d in (1, -1):
-                    near.add(int(s_ + (((c[m] + d) % L[m]) - c[m]) * stride[m]))
-        near = np.array(sorted(near))
-        res = np.zeros_like(bs[k])          # b - M x on the sites next to the samples
-        res[near] = bs[k][near] - (x[k][near] - kappa * W.dslash_w_sites(U, x[k], dims, near))
-        g5r = W.gamma5(res)
-        nres = W.gamma5(g5r[sites] - kappa * W.dslash_w_sites(U, g5r, dims, sites))   # M^dagger (b - M x)
-        g5b = W.gamma5(bs[k])
-        rhs = W.gamma5(g5b[sites] - kappa * W.dslash_w_sites(U, g5b, dims, sites))
-        assert np.linalg.norm(nres) / np.linalg.norm(rhs) <= 1e-9
+        assert _sampled_normal_residual(U, x[k], bs[k], dims, kappa, sites) <= 1e-9
     torch.cuda.empty_cache()
