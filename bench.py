@@ -1,9 +1,14 @@
 #!/usr/bin/env python
 """Benchmark: staggered even-odd CG (Dslash inside CG) on one GB300, through the C-ABI.
 
-One step = one pass of the whole hot path on one synthetic problem: pack the gauge field
-(qcd_load_links), run the even-odd CG to a relative true residual of 1e-10 with the fused
-Dslash/CG kernels, form y = D_oe x and recompute the FP64 true residual (qcd_cg_solve).
+Default workload (cg32_mixed): the 32^4 Haar lattice at m = 0.01. One step = one pass of the whole
+hot path: pack the gauge field at FP64 and FP32 recon-12 (qcd_load_links), run the mixed-precision
+even-odd CG (FP32 recon-12 recursion with the fused Dslash/CG kernels, FP64 reliable updates) to a
+true relative residual of 1e-10, form y = D_oe x and recompute the FP64 true residual
+(qcd_cg_solve). The same line carries the plain FP64, FP16 recon-12 and df64 solves of the same
+problem (speedups), each solution's residual recomputed by the oracle at sampled sites, each
+precision's operator alone, and the 24^4 x 16 RHS and 64-lattice batched solves with their
+speedups over one-by-one plain FP64 CG. Other workloads: --workload.
 
 value = Dslash GFLOP/s sustained inside the solve: 570 flop per output site of every
 half-lattice operator application the solve performs (2 per CG iteration, 2 more for y and
@@ -37,6 +42,13 @@ FLOP_PER_SITE = 570
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 WORKLOADS = {
+    # the headline: 32^4 Haar, m = 0.01, mixed FP32 recon-12 CG with FP64 reliable updates, with the
+    # plain FP64, FP16 and df64 solves, the operators alone and the batched solves on the same line
+    "cg32_mixed": dict(kind_solve="mixed32", dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10,
+                       inner="single12",
+                       desc="staggered 32^4 Haar SU(3), m=0.01, mixed CG: FP32 recon-12 inner, FP64 reliable updates "
+                            "every 100 iterations, to true rel. residual 1e-10 (vs plain FP64, FP16 recon-12 and "
+                            "df64 on the same lattice; 24^4 x 16 RHS and 64-lattice batches beside)"),
     # the 16^4 FP64 workload: Haar links, m = 0.1, plain FP64 even-odd CG
     "cg16_fp64": dict(dims=(16, 16, 16, 16), kind="haar", mass=0.1, tol=1e-10, inner="double",
                       desc="staggered 16^4 Haar SU(3), m=0.1, plain FP64 even-odd CG to true rel. residual 1e-10"),
@@ -90,7 +102,7 @@ WORKLOADS = {
                              desc="64 independent staggered lattices {4^4,6^4,8^4,8^3x16}, m in [0.02,0.5], one "
                                   "persistent clustered CG launch: FP32 recon-12 inner, FP64 reliable updates"),
 }
-DEFAULT_WORKLOAD = "cg16_fp64"
+DEFAULT_WORKLOAD = "cg32_mixed"
 PRECS = {"double": (0, 18), "single18": (1, 18), "single12": (1, 12), "half12": (2, 12), "df64": (3, 18)}
 DTYPE = {"double": "f64", "single18": "f32 (FP64 reliable updates)", "single12": "f32 (FP64 reliable updates)",
          "half12": "f16-storage/f32 (FP64 reliable updates)",
@@ -114,6 +126,14 @@ def _clock_sampler(device_uuid):
     except (OSError, ValueError):
         return None, f.name
     return p, f.name
+
+
+def _device_uuid(local):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        return None
 
 
 def _clock_summary(proc, path):
@@ -378,6 +398,315 @@ def run_gpu(args, wl):
     return out if rank == 0 else None
 
 
+# Algorithmic bytes per output site of one half-lattice operator launch (links once, every vector
+# read or written once) for the two operator launches of a CG iteration: K1 = links + p + ap; K2 =
+# links + ap + (p, r, x) read + (r, x) written (x at FP32 for the mixed precisions); and for the
+# operator alone (qcd_dslash: links + in + out).
+OP_BYTES = {  # name: (link bytes, field bytes, x bytes)
+    "double": (1152, 48, 48), "single18": (576, 24, 24), "single12": (384, 24, 24), "half12": (192, 16, 24),
+    "df64": (1152, 48, 48)}
+
+
+def _k1_k2_bytes(inner):
+    link_b, fld_b, x_b = OP_BYTES[inner]
+    return link_b + 2 * fld_b, link_b + fld_b + 2 * fld_b + x_b + fld_b + x_b
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def fp64_gemm_tflops(n=4096, reps=3):
+    """FP64 throughput measured on this GPU by a cuBLAS DGEMM (torch.matmul in float64, n^3):
+    the measured FP64 peak beside the derived one (2 FP64 FMA per SM per clock)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = torch.empty_like(a)
+    torch.matmul(a, b, out=c)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    del a, b, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def sampled_oracle_residual(U, x, b, dims, mass, n_sites=2000, seed=0):
+    """|b - A x| / |b| over `n_sites` random even sites, A applied by the FP64 oracle's site-local form."""
+    from oracle import staggered as S
+    rng = np.random.default_rng(seed)
+    V = U.shape[0]
+    cand = rng.choice(V, 3 * n_sites, replace=False)
+    sites = cand[S.parity_of_sites(dims, cand) == 0][:n_sites]
+    r = b[sites] - S.mdagm_sites(U, x, dims, mass, sites)
+    return float(np.linalg.norm(r) / np.linalg.norm(b[sites]))
+
+
+def run_gpu_mixed32(args, wl):
+    """32^4 Haar, m = 0.01: the mixed-precision even-odd CG (FP32 recon-12 recursion, FP64 reliable
+    updates) as the headline, with on the same line and the same lattice and source:
+      fp64      - the plain FP64 CG and the mixed solve's speedup over it;
+      half12 / df64 - the FP16+scale recon-12 and the df64 recursions;
+      accuracy  - each solution's FP64 residual recomputed by the oracle at sampled sites, and its
+                  distance to the plain FP64 GPU solution;
+      operators - each precision's half-lattice operator alone (qcd_dslash, back-to-back launches);
+      batched   - the 24^4 x 16 RHS and the 64-lattice solves and their speedups over one-by-one
+                  plain FP64 CG.
+    One timed step = qcd_load_links (FP64 and FP32 recon-12) + qcd_cg_solve (CG, y, true residual)."""
+    import torch
+
+    from paper_1311_2719_gb300 import inputs as I
+    from paper_1311_2719_gb300 import qcd as Q
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dims, mass, tol = wl["dims"], wl["mass"], wl["tol"]
+    U = I.make_links(dims, kind=wl["kind"], seed=1)
+    b = I.make_source(dims, seed=2)
+    Vh = U.shape[0] // 2
+    peaks = _measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    leg_steps = max(1, min(args.steps, args.leg_steps))
+
+    stream = torch.cuda.Stream()
+    lat = Q.Lattice(dims)
+    U_host = torch.from_numpy(U).pin_memory()
+    b_host = torch.from_numpy(b).pin_memory()
+    U_dev = U_host.to("cuda")
+    b_dev = b_host.to("cuda")
+    x_dev = torch.zeros_like(b_dev)
+    y_dev = torch.zeros_like(b_dev)
+    x_host = torch.empty_like(b_host).pin_memory()
+    y_host = torch.empty_like(b_host).pin_memory()
+    pack_of = {"double": (0, 18), "single12": (1, 12), "half12": (2, 12), "df64": (3, 18)}
+    bufs = {p: lat.empty_bytes(Q.qcd_links_bytes(lat.handle, p, r)) for p, r in pack_of.values()}
+    opts = Q.qcd_solver_opts_default()
+    ws = {}
+    for name, (p, r) in pack_of.items():
+        opts.prec_inner, opts.recon_inner = p, r
+        ws[name] = lat.empty_bytes(Q.qcd_workspace_bytes(lat.handle, opts, 1))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step(inner, host_io=False, profile=False):
+        p_in, r_in = pack_of[inner]
+        opts.prec_inner, opts.recon_inner = p_in, r_in
+        opts.profile = 1 if profile else 0
+        launches = 0
+        with torch.cuda.stream(stream):
+            if host_io:
+                U_dev.copy_(U_host, non_blocking=True)
+                b_dev.copy_(b_host, non_blocking=True)
+            for p, r in sorted({(0, 18), (p_in, r_in)}):
+                Q.qcd_load_links(lat.handle, U_dev, bufs[p], p, r, stream)
+                launches += 1
+            rc, info = Q.qcd_cg_solve(lat.handle, x_dev, b_dev, mass, tol, 100000, opts, ws[inner], y_dev,
+                                      stream=stream)
+            if host_io:
+                x_host.copy_(x_dev, non_blocking=True)
+                y_host.copy_(y_dev, non_blocking=True)
+        if rc != Q.QCD_OK:
+            raise RuntimeError(f"{inner} solve failed: {Q.qcd_status_string(rc)} {info}")
+        info["launches"] = launches + info["kernel_launches"]
+        return info
+
+    def timed(inner, n, host_io=False, profile=False):
+        ms, infos = [], []
+        for _ in range(n):
+            flush.fill_(1)  # evict L2 between steps (outside the timed events)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step(inner, host_io, profile))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, infos
+
+    def flops_of(infos):
+        return sum(FLOP_PER_SITE * Vh * _half_dslash_count(i) for i in infos)
+
+    # ---- headline: the mixed FP32 recon-12 solve
+    head = "single12"
+    for _ in range(args.warmup):
+        step(head)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    proc, cpath = _clock_sampler(_device_uuid(local))
+    time.sleep(0.3)
+    t_wall = time.perf_counter()
+    ms, infos = timed(head, args.steps)
+    t_wall = time.perf_counter() - t_wall
+    clocks = _clock_summary(proc, cpath)
+    if world > 1:
+        dist.barrier()
+    x_mixed = x_dev.cpu().numpy()
+    ms_e2e, infos_e2e = timed(head, leg_steps, host_io=True)
+    ms_prof, infos_prof = timed(head, 1, profile=True)
+    (total_ms, total_e2e), (fl, fl_e2e) = reduce_over_ranks([sum(ms), sum(ms_e2e)], [flops_of(infos), flops_of(infos_e2e)])
+    value = fl / (total_ms * 1e-3) / 1e9
+    e2e_value = fl_e2e / (total_e2e * 1e-3) / 1e9
+    t_mixed = sum(ms) / len(ms)
+
+    # ---- the other recursions on the same lattice and source
+    legs, sols = {}, {head: x_mixed}
+    for inner in ("double", "half12", "df64"):
+        if inner == "df64" and args.no_variant:
+            continue
+        step(inner)
+        ms_l, inf_l = timed(inner, leg_steps)
+        sols[inner] = x_dev.cpu().numpy()
+        i = inf_l[-1]
+        legs[inner] = {"dtype": DTYPE[inner], "ms_per_step": round(sum(ms_l) / len(ms_l), 4), "steps": len(ms_l),
+                       "value": round(flops_of(inf_l) / (sum(ms_l) * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+                       "iterations": i["iterations"], "reliable_updates": i["reliable_updates"],
+                       "true_rel_residual": i["true_rel_residual"]}
+    t_fp64 = legs["double"]["ms_per_step"]
+
+    # ---- accuracy of every solution: oracle residual at sampled sites, distance to the FP64 solution
+    x64 = sols["double"]
+    accuracy = {}
+    for inner, xs in sols.items():
+        accuracy[inner] = {"oracle_rel_residual_2000_even_sites": sampled_oracle_residual(U, xs, b, dims, mass),
+                           "rel_diff_vs_plain_fp64_gpu_solution": float(np.linalg.norm(xs - x64) / np.linalg.norm(x64))}
+
+    # ---- the half-lattice operator alone, per precision: back-to-back qcd_dslash launches that
+    # alternate between two lattices with their own links (so that the links stream from DRAM even
+    # where one precision's links would fit in L2), CUDA events around the whole loop
+    lat2 = Q.Lattice(dims)
+    bufs2 = {p: lat2.empty_bytes(Q.qcd_links_bytes(lat2.handle, p, r)) for p, r in pack_of.values()}
+    operators = {}
+    fp64_meas = fp64_gemm_tflops()
+    n_op = 40
+    for name, (p, r) in pack_of.items():
+        with torch.cuda.stream(stream):
+            for L_, B_ in ((lat, bufs), (lat2, bufs2)):
+                Q.qcd_load_links(L_.handle, U_dev, B_[p], p, r, stream)
+            fin = lat.field(p)
+            Q.qcd_pack_field(lat.handle, fin, b_dev, Q.QCD_EVEN, p, stream)
+            fouts = [lat.field(p), lat2.field(p)]
+            for k in range(4):  # warm-up
+                Q.qcd_dslash((lat, lat2)[k & 1].handle, fouts[k & 1], fin, Q.QCD_ODD, p, stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(n_op):
+            Q.qcd_dslash((lat, lat2)[k & 1].handle, fouts[k & 1], fin, Q.QCD_ODD, p, stream)
+        e1.record(stream)
+        e1.synchronize()
+        t_us = e0.elapsed_time(e1) * 1e3 / n_op
+        link_b, fld_b, _ = OP_BYTES[name]
+        bps = link_b + 2 * fld_b
+        gbs = bps * Vh / (t_us * 1e-6) / 1e9
+        tf = FLOP_PER_SITE * Vh / (t_us * 1e-6) / 1e12
+        o = {"us_per_launch": round(t_us, 3), "gflops": round(tf * 1e3, 1), "alg_bytes_per_site": bps,
+             "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
+        if name == "double":
+            o.update({"frac_fp64_peak_derived": round(tf / FP64_PEAK_TFLOPS, 4),
+                      "frac_fp64_peak_measured_dgemm": round(tf / fp64_meas, 4),
+                      "bound": "FP64 pipe (570 flop vs 1248 B per site; the FP64 pipe caps it near "
+                               f"{FP64_PEAK_TFLOPS / FLOP_PER_SITE * 1e3 * bps:.0f} GB/s)"})
+        elif name == "df64":
+            o["note"] = ("df64 = float-float pairs (48-bit significand, FP32's 8-bit exponent): an inner-solver "
+                         "precision narrower than FP64, run on the FP32 pipes")
+        operators[name] = o
+        del fin, fouts
+    del lat2, bufs2
+
+    # ---- roofline of the dominant kernel family: every half-lattice operator launch of the timed
+    # step (the FP32 recon-12 K1/K2 of the recursion and the FP64 ones of the reliable updates, y
+    # and the true residual), charged with ALL of the step's time: a lower bound on their rate that
+    # agrees by construction with the step time.
+    i = infos[-1]
+    n32 = 2 * i["iterations"]
+    n_all = _half_dslash_count(i)
+    n64 = n_all - n32
+    k1_32, k2_32 = _k1_k2_bytes(head)
+    k1_64, k2_64 = _k1_k2_bytes("double")
+    alg_step = Vh * (i["iterations"] * (k1_32 + k2_32) + n64 / 2 * (k1_64 + k2_64))
+    per_launch_us = t_mixed * 1e3 / n_all
+    achieved = alg_step / (t_mixed * 1e-3) / 1e9
+    d_ms, d_n = infos_prof[-1]["dslash_ms"], infos_prof[-1]["dslash_launches"]
+    roofline = {
+        "bound": "hbm", "kernel": "dslash_kernel (CG K1+K2 launches, FP32 recon-12; FP64 in the reliable updates)",
+        "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+        "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
+        "traffic": ncu_traffic(args.workload),
+        "method": "all of the timed step's time charged to its operator launches (a lower bound on the "
+                  "kernels' rate); per-launch bytes = the mean of K1 and K2 at the launch's precision",
+        "alg_bytes_per_site_k1_k2": [k1_32, k2_32], "alg_bytes_per_site_k1_k2_fp64": [k1_64, k2_64],
+        "alg_bytes_per_step": round(alg_step), "alg_bytes_per_launch_fp32": (k1_32 + k2_32) / 2 * Vh,
+        "check": {"operator_launches": n_all, "fp32_launches": n32, "fp64_launches": n64,
+                  "per_launch_us": round(per_launch_us, 3),
+                  "launches_x_per_launch_ms": round(n_all * per_launch_us / 1e3, 4),
+                  "ms_per_step": round(t_mixed, 4),
+                  "ok": bool(n_all * per_launch_us / 1e3 <= t_mixed * (1 + 1e-9))},
+        "direct_launch_events": {"us_per_launch": round(d_ms / d_n * 1e3, 3), "launches": d_n,
+                                 "note": "a separate pass of direct launches with CUDA events around each "
+                                         "operator launch (includes event overhead)"}}
+
+    # ---- config 4: the multi-RHS and many-lattice solves (their own lattices and sources)
+    batched = {}
+    if not args.no_batched:
+        for key in ("mrhs24_single12", "batch64_single12"):
+            bl = batched_leg(WORKLOADS[key], leg_steps if key.startswith("mrhs") else max(leg_steps, 5), 1, False,
+                             key, world, local, fp64_steps=max(1, min(leg_steps, 2)), sample_clocks=False)
+            batched[key] = {"workload": WORKLOADS[key]["desc"], "value": bl["value"], "unit": bl["unit"],
+                            "ms_per_step": bl["ms_per_step"], "steps": bl["steps"], "cg": bl["cg"],
+                            "roofline": bl["roofline"], "gpu_launches": bl["gpu_launches"]}
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_mixed, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[head],
+        "data": "synthetic (seeded Haar SU(3) links, Gaussian source)",
+        "config": {"workload": wl["desc"], "dims": list(dims), "mass": mass, "tol": tol, "inner": head,
+                   "reliable_update_interval": 100, "parallelism": f"replicas x{world} (no sharding)",
+                   "l2": "flushed before every step (512 MB write, outside the timed events)",
+                   "step": "qcd_load_links (FP64 + FP32 recon-12) + qcd_cg_solve (CG, y = D_oe x, FP64 true residual)",
+                   "legs": f"fp64/half12/df64 solves, e2e and batched: {leg_steps} timed steps each after one untimed"},
+        "cg": {"iterations": i["iterations"], "true_rel_residual": i["true_rel_residual"],
+               "reliable_updates": i["reliable_updates"], "time_to_solution_ms": round(t_mixed, 4),
+               "half_dslash_per_solve": n_all, "plain_fp64_ms": t_fp64,
+               "speedup_vs_fp64": round(t_fp64 / t_mixed, 3),
+               "speedup_vs_fp64_half12": round(t_fp64 / legs["half12"]["ms_per_step"], 3)},
+        "legs": legs,
+        "accuracy": accuracy,
+        "roofline": roofline,
+        "operators": operators,
+        "fp64_peak": {"derived_tflops": round(FP64_PEAK_TFLOPS, 4), "measured_dgemm_tflops": round(fp64_meas, 4),
+                      "note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; measured: cuBLAS DGEMM 4096^3 "
+                              "(torch.matmul float64), best of 3"},
+        "batched": batched,
+        "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int(U_host.numel() * 16 + b_host.numel() * 16),
+                "d2h_bytes_per_step": int(x_host.numel() * 16 + y_host.numel() * 16),
+                "ms_per_step": round(total_e2e / len(ms_e2e), 4), "steps": len(ms_e2e)},
+        "gpu_launches": int(sum(i_["launches"] for i_ in infos)),
+        "clocks": clocks,
+        "wall_s_timed_region": round(t_wall, 4),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_all_cores(wl, U, b)
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
 def run_gpu_batched(args, wl):
     """Multi-RHS (one lattice, nrhs sources) or multi-lattice (one persistent launch) workloads.
 
@@ -395,6 +724,21 @@ def run_gpu_batched(args, wl):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = batched_leg(wl, args.steps, args.warmup, args.tune, args.workload, world, local)
+    if world > 1:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def batched_leg(wl, steps, warmup, tune, workload_key, world=1, local=0, fp64_steps=3, sample_clocks=True):
+    """The multi-RHS or many-lattice solve of `wl`: `warmup` untimed and `steps` timed steps (L2
+    flushed before each), then the same problems one by one with plain FP64 CG (`fp64_steps` timed
+    after one untimed). Returns the bench line's fields (whole-job value over ranks)."""
+    import torch
+
+    from paper_1311_2719_gb300 import inputs as I
+    from paper_1311_2719_gb300 import qcd as Q
+
     inner = wl["inner"]
     prec_in, recon_in = PRECS[inner]
     tol = wl["tol"]
@@ -464,7 +808,7 @@ def run_gpu_batched(args, wl):
         return ms, outs
 
     tuned = None
-    if args.tune:
+    if tune:
         with torch.cuda.stream(stream):
             load_links()
             if wl["kind_solve"] == "mrhs":
@@ -475,20 +819,19 @@ def run_gpu_batched(args, wl):
                                             stream=stream)
                 tuned = {"cluster_size": c, "block_size": blk}
         torch.cuda.synchronize()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
-    except Exception:
-        uuid = None
-    proc, cpath = _clock_sampler(uuid)
-    time.sleep(0.3)
-    ms, outs = timed(step, args.steps)
-    clocks = _clock_summary(proc, cpath)
+    clocks = None
+    if sample_clocks:
+        proc, cpath = _clock_sampler(_device_uuid(local))
+        time.sleep(0.3)
+    ms, outs = timed(step, steps)
+    if sample_clocks:
+        clocks = _clock_summary(proc, cpath)
 
     # the same problems, one by one, with plain FP64 CG on the GPU
     o64 = Q.qcd_solver_opts_default()
@@ -506,16 +849,16 @@ def run_gpu_batched(args, wl):
                         raise RuntimeError("FP64 reference solve failed")
         return 0
     fp64_step()
-    ms64, _ = timed(fp64_step, max(1, min(args.steps, 3)))
+    ms64, _ = timed(fp64_step, max(1, fp64_steps))
 
     (t_all,), (fl_all,) = reduce_over_ranks([sum(ms)], [sum(o[0] for o in outs)])
     value = fl_all / (t_all * 1e-3) / 1e9
     infos = outs[-1][1]
-    t_batched = sum(ms) / args.steps
+    t_batched = sum(ms) / steps
     t_fp64 = sum(ms64) / len(ms64)
     out = {
-        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t_batched, 4), "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(t_batched, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[inner], "data": "synthetic (seeded Haar SU(3) links, Gaussian sources)",
         "config": {"workload": wl["desc"], "problems": len(specs) * nrhs, "tol": tol, "inner": inner,
                    "parallelism": f"replicas x{world} (no sharding)",
@@ -526,7 +869,7 @@ def run_gpu_batched(args, wl):
                "max_iterations": max(i["iterations"] for i in infos),
                "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
                "reliable_updates": sum(i["reliable_updates"] for i in infos),
-               "plain_fp64_gpu_cg_ms": round(t_fp64, 4),
+               "plain_fp64_gpu_cg_ms": round(t_fp64, 4), "plain_fp64_steps": len(ms64),
                "speedup_vs_plain_fp64_gpu_cg": round(t_fp64 / t_batched, 3)},
         "gpu_launches": int(sum(o[2] for o in outs)),
         "clocks": clocks,
@@ -558,7 +901,7 @@ def run_gpu_batched(args, wl):
         ach = alg / (d_ms * 1e-3) / 1e9
         out["roofline"] = {"bound": "hbm", "kernel": "dslash_mrhs_cg_kernel (K1+K2 launches)", "achieved": round(ach, 1),
                            "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
-                           "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": ncu_traffic(args.workload),
+                           "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": ncu_traffic(workload_key),
                            "alg_bytes_per_launch": round(alg / d_n), "avg_launch_us": round(d_ms / d_n * 1e3, 3),
                            "alg_bytes_per_site": {"links_per_launch": link_b, "k1_per_rhs": k1_rhs, "k2_per_rhs": k2_rhs},
                            "note": f"the links ({Q.qcd_links_bytes(lats[0].handle, prec_in, recon_in) / 1e6:.0f} MB) "
@@ -570,12 +913,10 @@ def run_gpu_batched(args, wl):
         ach = alg / (t_batched * 1e-3) / 1e9
         out["roofline"] = {"bound": "latency", "kernel": "batched_cg_kernel (whole batch, one launch)",
                            "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
-                           "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": ncu_traffic(args.workload),
+                           "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)", "traffic": ncu_traffic(workload_key),
                            "alg_bytes_per_launch": round(alg),
                            "note": "L2-resident lattices; every CG step ends in a cluster barrier: latency-bound by design"}
-    if world > 1:
-        dist.destroy_process_group()
-    return out if rank == 0 else None
+    return out
 
 
 WILSON_FLOP_PER_SITE = 1320
@@ -1113,6 +1454,88 @@ def cpu_baseline(wl, iters):
                       f"residual ({dt:.1f} s), algorithmic 570 flop/site per half-lattice operator"}
 
 
+# ---- the FP64 oracle on all host cores: one process per core (spawned, never forked after the GPU
+# is in use), each applying the oracle's normal operator A = m^2 - D_eo D_oe (its site-local form)
+# to a slice of the even sites of the same lattice; the links and the source are shared read-only
+# through a memory-mapped file.
+_ORACLE_SHARED = {}
+
+
+def _oracle_worker_init(path_u, path_b, dims, mass):
+    _ORACLE_SHARED.update(U=np.load(path_u, mmap_mode="r"), b=np.load(path_b, mmap_mode="r"), dims=tuple(dims),
+                          mass=mass)
+
+
+def _oracle_worker_apply(sites):
+    from oracle import staggered as S
+    d = _ORACLE_SHARED
+    S.mdagm_sites(d["U"], d["b"], d["dims"], d["mass"], sites)
+    return len(sites)
+
+
+class OraclePool:
+    """`cores` oracle processes over the even sites of one lattice; pass() applies A everywhere once."""
+
+    def __init__(self, U, b, dims, mass, cores=None):
+        import multiprocessing as mp
+        from oracle import staggered as S
+        self.cores = cores or os.cpu_count() or 1
+        self.dir = tempfile.mkdtemp(prefix="oracle_")
+        pu, pb = os.path.join(self.dir, "U.npy"), os.path.join(self.dir, "b.npy")
+        np.save(pu, U)
+        np.save(pb, b)
+        V = U.shape[0]
+        even = np.nonzero(S.parity_of_sites(dims, np.arange(V)) == 0)[0]
+        self.n_even = len(even)
+        self.slices = np.array_split(even, self.cores)
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"  # one thread per process: the process count is the core count
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init,
+                                                     initargs=(pu, pb, tuple(dims), mass))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run_pass(self):
+        t0 = time.perf_counter()
+        done = sum(self.pool.map(_oracle_worker_apply, self.slices, chunksize=1))
+        return 2 * FLOP_PER_SITE * done, time.perf_counter() - t0
+
+    def close(self):
+        import shutil
+        self.pool.close()
+        self.pool.join()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def cpu_baseline_all_cores(wl, U, b, min_seconds=8.0):
+    """The oracle as it stands on the host: all cores (one process each) applying A over the whole
+    lattice, repeated for at least `min_seconds`; and, beside it, one thread running the oracle CG
+    (first iteration + y + true residual) on the same lattice."""
+    pool = OraclePool(U, b, wl["dims"], wl["mass"])
+    try:
+        pool.run_pass()  # warm-up: worker start-up, page-in of the mapped links
+        fl, dt, passes = 0.0, 0.0, 0
+        while dt < min_seconds:
+            f, t = pool.run_pass()
+            fl, dt, passes = fl + f, dt + t, passes + 1
+    finally:
+        pool.close()
+    f1, dt1, n1 = _oracle_sample(wl, 1, U, b)
+    return {"value": round(fl / dt / 1e9, 4), "unit": "GFLOP/s", "cores": pool.cores, "kind": "oracle",
+            "sample": f"FP64 numpy oracle normal operator A = m^2 - D_eo D_oe (site-local form) over all "
+                      f"{pool.n_even} even sites of the {tuple(wl['dims'])} lattice, {passes} passes ({dt:.1f} s) on "
+                      f"{pool.cores} processes of one thread; 1140 flop per even site",
+            "single_thread": {"value": round(f1 / dt1 / 1e9, 4), "unit": "GFLOP/s", "cores": 1,
+                              "sample": f"FP64 numpy oracle CG on the same lattice: {n1} iteration + y + true "
+                                        f"residual ({dt1:.1f} s), 570 flop/site per half-lattice operator"}}
+
+
 def run_reference(args, wl):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload per step (rank 0 only)."""
     rank, world, _ = _env_rank()
@@ -1121,6 +1544,32 @@ def run_reference(args, wl):
     from paper_1311_2719_gb300 import inputs as I
 
     kind = wl.get("kind_solve")
+    if kind == "mixed32":
+        dims = wl["dims"]
+        U = I.make_links(dims, kind=wl["kind"], seed=1)
+        b = I.make_source(dims, seed=2)
+        pool = OraclePool(U, b, dims, wl["mass"])
+        pool.run_pass()
+        for _ in range(args.warmup):
+            pool.run_pass()
+        tot_f, tot_t = 0.0, 0.0
+        for _ in range(args.steps):
+            f, t = pool.run_pass()
+            tot_f, tot_t = tot_f + f, tot_t + t
+        pool.close()
+        v = tot_f / tot_t / 1e9
+        what = (f"each step: FP64 numpy oracle normal operator A = m^2 - D_eo D_oe (site-local form) over all "
+                f"{pool.n_even} even sites of the {dims} lattice, on {pool.cores} processes of one thread; "
+                f"1140 flop per even site")
+        return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 2),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded Haar SU(3) links, Gaussian source)",
+                "config": {"workload": wl["desc"], "tol": wl["tol"], "dims": list(dims), "mass": wl["mass"],
+                           "parallelism": "cpu oracle, rank 0 only"},
+                "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": pool.cores, "kind": "oracle",
+                                 "sample": what},
+                "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if kind == "wilson":
         from oracle import wilson as Wo
         dims = wl["dims"]
@@ -1194,7 +1643,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-iters", type=int, default=64, help="oracle CG iterations timed for cpu_baseline")
@@ -1202,6 +1651,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune", action="store_true", help="run the autotuner before the batched workloads")
     ap.add_argument("--no-variant", action="store_true", help="skip the df64 run beside an FP64 workload")
+    ap.add_argument("--leg-steps", type=int, default=3,
+                    help="timed steps of each side measurement of the cg32_mixed workload (after one untimed)")
+    ap.add_argument("--no-batched", action="store_true", help="cg32_mixed: skip the batched solves")
     ap.add_argument("--reliable-delta", type=float, default=None,
                     help="mixed Wilson CGNR: reliable-update threshold (default: the workload's, else the library's)")
     args = ap.parse_args()
@@ -1210,6 +1662,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         out = run_reference(args, wl)
+    elif wl.get("kind_solve") == "mixed32":
+        out = run_gpu_mixed32(args, wl)
     elif wl.get("kind_solve") in ("mrhs", "batched"):
         out = run_gpu_batched(args, wl)
     elif wl.get("kind_solve") == "wilson":

@@ -6,11 +6,13 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import bench  # noqa: E402
 
 
 def test_workloads_are_complete():
-    kinds = {"cg", "mrhs", "batched", "wilson", "full", "force"}
+    kinds = {"cg", "mixed32", "mrhs", "batched", "wilson", "full", "force"}
     for name, wl in bench.WORKLOADS.items():
         assert wl["desc"], name
         assert wl.get("kind_solve", "cg") in kinds, name
@@ -54,3 +56,47 @@ def test_source_hash_covers_names_and_contents(tmp_path, monkeypatch):
     assert h != bench.sources_sha(["a.cuh"])
     (csrc / "b.cuh").write_text("y ")
     assert h != bench.sources_sha(["a.cuh", "b.cuh"])
+
+
+def test_default_workload_is_the_32_4_mixed_solve():
+    wl = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    assert wl["kind_solve"] == "mixed32" and wl["dims"] == (32, 32, 32, 32)
+    assert wl["inner"] == "single12" and wl["mass"] == 0.01 and wl["tol"] == 1e-10
+
+
+def test_k1_k2_bytes_match_the_per_site_table():
+    # FP64 K1 = 1152 + 2*48, K2 = 1152 + 48 + 2*48 + 48 + 48 + 48; FP32 recon-12 and FP16 recon-12
+    assert bench._k1_k2_bytes("double") == (1248, 1440)
+    assert bench._k1_k2_bytes("single12") == (432, 528)
+    assert bench._k1_k2_bytes("half12") == (224, 304)
+
+
+def test_oracle_pool_applies_a_over_every_even_site_on_several_processes():
+    """The all-core oracle baseline: one spawned process per core, each applying the oracle's A to
+    a slice of the even sites; together they cover the lattice once per pass."""
+    from oracle import staggered as S
+    from paper_1311_2719_gb300 import inputs as I
+    dims = (4, 4, 4, 4)
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    pool = bench.OraclePool(U, b, dims, 0.1, cores=2)
+    try:
+        flops, dt = pool.run_pass()
+    finally:
+        pool.close()
+    assert pool.cores == 2 and pool.n_even == S.volume(dims) // 2
+    assert sorted(np.concatenate(pool.slices).tolist()) == np.nonzero(S.parity(dims) == 0)[0].tolist()
+    assert flops == 2 * bench.FLOP_PER_SITE * pool.n_even and dt > 0
+    assert bench._oracle_worker_apply  # importable by the spawned workers
+
+
+def test_sampled_oracle_residual_of_an_exact_solution_is_its_scale():
+    """x = (1 - eps) A^-1 b leaves b - A x = eps b at every site: the sampled residual is eps."""
+    from oracle import staggered as S
+    from paper_1311_2719_gb300 import inputs as I
+    dims, m, eps = (4, 4, 4, 4), 0.5, 1e-3
+    U = I.make_links(dims, kind="haar", seed=1)
+    b = I.make_source(dims, seed=2)
+    ref = S.cg_solve(U, b, dims, m, tol=1e-14, max_iter=2000)
+    got = bench.sampled_oracle_residual(U, (1 - eps) * ref["x"], b, dims, m, n_sites=40)
+    assert abs(got - eps) <= 1e-10
