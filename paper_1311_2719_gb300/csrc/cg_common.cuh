@@ -585,12 +585,20 @@ __device__ __forceinline__ bool mrhs_arrive(double (&v)[RB], int r0, int nrhs, d
 }
 
 // In the last block: tot[r] = sum over blocks of partials[r][.] in block order (deterministic).
+// Four right-hand sides at a time, so that their loads are in flight together; each total is summed
+// in the same order as a single-RHS reduction over the same grid.
 __device__ __forceinline__ void mrhs_totals(int nrhs, const double* partials, double* tot_smem) {
   __threadfence();
-  for (int r = 0; r < nrhs; ++r) {
-    double s[1] = {0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[0] += __ldcg(partials + (size_t)r * kMaxPartials + b);
-    block_sum<1>(s);
+  int r = 0;
+  for (; r + 4 <= nrhs; r += 4) {
+    double s[4];
+    sum_partials<4>(partials + (size_t)r * kMaxPartials, (int)gridDim.x, s);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 4; ++q) tot_smem[r + q] = s[q];
+  }
+  for (; r < nrhs; ++r) {
+    double s[1];
+    sum_partials<1>(partials + (size_t)r * kMaxPartials, (int)gridDim.x, s);
     if (threadIdx.x == 0) tot_smem[r] = s[0];
   }
   __syncthreads();
