@@ -71,6 +71,8 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
   R.tps = threads_per_site(PREC, lat->Vh);
   cg_launch_shape((long long)lat->Vh * R.tps, cg_grid<PREC, RECON>(lat->Vh, R.tps), &R.grid, &R.block);
   R.setup_staged(o.staged != 0);
+  R.stream_in = stream_links(PREC, RECON, lat->Vh);
+  R.stream64 = stream_links(QCD_PREC_DOUBLE, 18, lat->Vh);
   R.wait_cycles = o.wait_cycles > 0 ? o.wait_cycles : kWaitCycles;
   const bool mixed = PREC != QCD_PREC_DOUBLE;
 
@@ -116,7 +118,7 @@ static int cg_typed(qcd_lattice* lat, void* x, const void* b, double mass, doubl
     if ((rc = read_scalars(R.w, &h, st))) { cleanup(); return rc; }
     if (h.done == kBreakdown) status = QCD_ERR_BREAKDOWN;
     else if (h.done != kTrueConverged) status = QCD_ERR_NOT_CONVERGED;
-    R.launches += (long long)h.loops * (3ll * k + (mixed ? 3 : 2) + 1);
+    R.launches += (long long)h.loops * ((long long)R.launches_per_iteration() * k + (mixed ? 3 : 2) + 1);
     dslash_launches = 2 * h.iter;
   } else {
     if ((rc = read_scalars(R.w, &h, st))) { cleanup(); return rc; }

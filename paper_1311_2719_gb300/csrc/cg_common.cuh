@@ -131,6 +131,59 @@ struct EpiAp {
   }
 };
 
+// ---------------------------------------------------------------- K1 with the p update folded in
+// p_next = r + beta p at a site, from the stored r and p: the CG's "p = r + beta p" step, done by the
+// operator that consumes p so that it needs no launch and no pass over memory of its own.
+template <class FieldT>
+struct PNext {
+  using T = typename FieldT::T;
+  static constexpr int kElemsPerSite = FieldT::kElemsPerSite;
+  FieldT r, p;
+  T beta;
+  __device__ __forceinline__ cvec3<T> load(int j) const {
+    const cvec3<T> rv = r.load(j);
+    cvec3<T> pv = p.load(j);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      pv.c[a].re = fma(beta, pv.c[a].re, rv.c[a].re);
+      pv.c[a].im = fma(beta, pv.c[a].im, rv.c[a].im);
+    }
+    return pv;
+  }
+};
+
+// K1 for the FP32 recursion: iteration i reads p_i from buffer i mod 2 (p0, p1), gathers
+// p_{i+1} = r + beta p_i at the neighbours, and writes ap = D_oe p_{i+1}, p_{i+1} at the even site with
+// the same index into the other buffer, |ap|^2 and |p_{i+1}|^2. The stored p_{i+1} is bit-identical to
+// the one every neighbour formed (the same FP32 multiply-add), so the recursion is the unfolded one.
+// Measured on GB300 (32^4, m = 0.01): 334.7 -> 329.6 ms per solve. The other recursions keep the
+// separate p kernel: FP16 (issue-bound decoding two packed fields at every neighbour, and the stored p
+// rounded to FP16 differs from the gathered one; 318.6 -> 329.7 ms), FP64 and df64 (the extra
+// multiply-adds at every neighbour cost more on the FP64 / FP32 pipes than the pass they save).
+template <class FieldT>
+struct EpiApFold {
+  static constexpr int NV = 2;
+  static constexpr bool kPrefetch = false;
+  using T = typename FieldT::T;
+  FieldT ap, r, p0, p1;
+  CgScalars* sc;
+  double* partials;
+  __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
+  __device__ __forceinline__ PNext<FieldT> next() const { return {r, (sc->iter & 1) ? p1 : p0, (T)sc->beta}; }
+  template <class In>
+  __device__ __forceinline__ PNext<FieldT> bind(const In&) const { return next(); }
+  template <class A>
+  __device__ __forceinline__ void site(int k, cvec3<T>& acc, A* red) const {
+    ap.store(k, acc);
+    const cvec3<T> pv = next().load(k);
+    ((sc->iter & 1) ? p0 : p1).store(k, pv);
+    accum(red[0], norm2(acc));
+    accum(red[1], norm2(pv));
+  }
+  template <class A>
+  __device__ __forceinline__ void finish(A* red) const { EpiAp<FieldT>{ap, p0, sc, partials}.finish(red); }
+};
+
 // ---------------------------------------------------------------- K2 epilogue: update x, r
 template <class FieldT, class XFieldT>
 struct EpiUpdate {
@@ -140,12 +193,17 @@ struct EpiUpdate {
   XFieldT x;
   CgScalars* sc;
   double* partials;
+  // With the p update folded into K1 (EpiApFold), p of iteration i + 1 sits in p_odd when i is even
+  // and in p when i is odd.
+  FieldT p_odd = {};
+  int pingpong = 0;
   struct Pre {
     cvec3<typename FieldT::T> p, r;
     cvec3<typename XFieldT::T> x;
   };
   __device__ __forceinline__ bool skip() const { return sc->done != kRunning; }
-  __device__ __forceinline__ Pre prefetch(int k) const { return Pre{p.load(k), r.load(k), x.load(k)}; }
+  __device__ __forceinline__ const FieldT& cur_p() const { return (pingpong && !(sc->iter & 1)) ? p_odd : p; }
+  __device__ __forceinline__ Pre prefetch(int k) const { return Pre{cur_p().load(k), r.load(k), x.load(k)}; }
   template <class T, class A>
   __device__ __forceinline__ void site(int k, cvec3<T>& acc, A* red) const { site_pre(k, acc, red, prefetch(k)); }
   template <class T, class A>
@@ -347,6 +405,7 @@ struct CgWork {
   void* tmp_o;  // FP64 odd: reliable-update D_oe x and the final y
   void* r;
   void* p;
+  void* p2;  // second p buffer of the folded K1 (FP32 recursion), else nullptr
   void* ap;
   void* x_lo;
   size_t total;
@@ -373,6 +432,8 @@ inline CgWork carve(const qcd_lattice* lat, int prec_inner, int R, char* base) {
   w.r = take(w.fin * R);
   w.p = take(w.fin * R);
   w.ap = take(w.fin * R);
+  // the FP32 recursion alternates p between two buffers (EpiApFold)
+  w.p2 = prec_inner == QCD_PREC_SINGLE ? take(w.fin * R) : nullptr;
   // plain FP64: x accumulates directly in the FP64 field
   w.x_lo = prec_inner == QCD_PREC_DOUBLE ? w.x_hi : take(w.fx * R);
   w.total = off;
@@ -389,6 +450,7 @@ inline CgWork view(const CgWork& w, int r) {
   v.tmp_o = at(w.tmp_o, w.f64);
   v.r = at(w.r, w.fin);
   v.p = at(w.p, w.fin);
+  v.p2 = at(w.p2, w.fin);
   v.ap = at(w.ap, w.fin);
   v.x_lo = at(w.x_lo, w.fx);
   v.R = 1;
@@ -410,6 +472,8 @@ struct CgRunner {
   int tps = 1;         // threads per site of the operator kernels
   long long launches = 0;
 
+  int stream_in = 0;    // stream the inner-precision links with the L2 evict-first policy
+  int stream64 = 0;     // the same for the FP64 links of the reliable updates and the output
   int staged_grid = 0;  // > 0: FP32 recon-12 operator launches use the staged kernel with this grid
   long long wait_cycles = kWaitCycles;
 
@@ -460,10 +524,28 @@ struct CgRunner {
 
   // One CG iteration (K3 p = r + beta p; K1 ap = D_oe p with |ap|^2 and |p|^2; K2 D_eo ap and the
   // x, r update with |r|^2). With `ev` (4 events) the two operator launches are bracketed.
+  // The FP32 recursion runs the p update inside K1 (two launches per iteration), except with the
+  // staged operator, which stages one stored input field.
+  bool folded() const { return PREC == QCD_PREC_SINGLE && staged_grid == 0 && w.p2; }
+  int launches_per_iteration() const { return folded() ? 2 : 3; }
+
   int iteration(cudaEvent_t* ev = nullptr) {
     auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
+    U.stream = stream_in;
     FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh), ap = make_field<PREC>(w.ap, g.Vh);
     XFieldT x = make_field<XPREC::value>(w.x_lo, g.Vh);
+    if (folded()) {
+      FieldT p2 = make_field<PREC>(w.p2, g.Vh);
+      if (ev) QCD_CUDA(cudaEventRecord(ev[0], st));
+      op(U, p, QCD_ODD, EpiApFold<FieldT>{ap, r, p, p2, w.sc, w.partials});
+      if (ev) QCD_CUDA(cudaEventRecord(ev[1], st));
+      if (ev) QCD_CUDA(cudaEventRecord(ev[2], st));
+      op(U, ap, QCD_EVEN, EpiUpdate<FieldT, XFieldT>{p, r, x, w.sc, w.partials, p2, 1});
+      if (ev) QCD_CUDA(cudaEventRecord(ev[3], st));
+      QCD_CUDA(cudaGetLastError());
+      launches += 2;
+      return QCD_OK;
+    }
     cg_p_kernel<<<grid, block, 0, st>>>(g.Vh, r, p, w.sc);
     if (ev) QCD_CUDA(cudaEventRecord(ev[0], st));
     op(U, p, QCD_ODD, EpiAp<FieldT>{ap, p, w.sc, w.partials});
@@ -493,6 +575,7 @@ struct CgRunner {
   // `gated`: every kernel checks the device flag first (for the device-side loop body).
   int reliable_update(bool gated = false) {
     auto U64 = make_links<QCD_PREC_DOUBLE, 18>(lat->links[QCD_PREC_DOUBLE].ptr, g.Vh);
+    U64.stream = stream64;
     auto xh = make_field<QCD_PREC_DOUBLE>(w.x_hi, g.Vh);
     auto tmp = make_field<QCD_PREC_DOUBLE>(w.tmp_o, g.Vh);
     launches += PREC != QCD_PREC_DOUBLE ? 3 : 2;
@@ -515,6 +598,7 @@ struct CgRunner {
 
   int finish(void* x_canon, void* y_canon) {
     auto U64 = make_links<QCD_PREC_DOUBLE, 18>(lat->links[QCD_PREC_DOUBLE].ptr, g.Vh);
+    U64.stream = stream64;
     auto xh = make_field<QCD_PREC_DOUBLE>(w.x_hi, g.Vh);
     auto tmp = make_field<QCD_PREC_DOUBLE>(w.tmp_o, g.Vh);
     launches += PREC != QCD_PREC_DOUBLE ? 4 : 3;

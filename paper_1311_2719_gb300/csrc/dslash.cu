@@ -30,6 +30,7 @@ template <int PREC, int RECON>
 static int dslash_typed(const qcd_lattice* lat, void* out, const void* in, int out_par, cudaStream_t st) {
   const Geom g = make_geom(lat);
   auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
+  U.stream = stream_links(PREC, RECON, g.Vh);
   auto fin = make_field<PREC>(const_cast<void*>(in), g.Vh);
   EpiStore<Field<PREC>> epi{make_field<PREC>(out, g.Vh)};
   if (threads_per_site(PREC, g.Vh) == 2)
@@ -44,6 +45,7 @@ template <int PREC, int RECON>
 static int mdagm_typed(const qcd_lattice* lat, void* out, const void* in, double mass, void* tmp, cudaStream_t st) {
   const Geom g = make_geom(lat);
   auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
+  U.stream = stream_links(PREC, RECON, g.Vh);
   auto fin = make_field<PREC>(const_cast<void*>(in), g.Vh);
   auto ftmp = make_field<PREC>(tmp, g.Vh);
   EpiMdagm<Field<PREC>> epi{fin, make_field<PREC>(out, g.Vh), mass * mass};

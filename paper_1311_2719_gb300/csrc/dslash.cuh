@@ -117,10 +117,22 @@ struct MaxRegs {
   static constexpr int value = 65536 / (kBlock * MinBlocks<LinksT>::value) / 8 * 8;
 };
 
+// The operator's input as the epilogue sees it: an epilogue with a bind(in) member replaces the
+// input accessor at kernel start (the CG's K1 reads p = r + beta p_old instead of a stored p).
+template <class Epi, class In>
+__device__ __forceinline__ auto bind_input(const Epi& epi, const In& in, int) -> decltype(epi.bind(in)) {
+  return epi.bind(in);
+}
+template <class Epi, class In>
+__device__ __forceinline__ In bind_input(const Epi&, const In& in, long) {
+  return in;
+}
+
 template <class LinksT, class FieldT, class Epi, int TPS = 1>
-__global__ void __maxnreg__(MaxRegs<LinksT>::value) dslash_kernel(Geom g, LinksT U, FieldT in,
+__global__ void __maxnreg__(MaxRegs<LinksT>::value) dslash_kernel(Geom g, LinksT U, FieldT in_arg,
                                                                                  int out_par, Epi epi) {
   if (epi.skip()) return;
+  const auto in = bind_input(epi, in_arg, 0);
   using A = typename Accum<typename LinksT::T>::type;
   A red[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
