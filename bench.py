@@ -407,9 +407,12 @@ OP_BYTES = {  # name: (link bytes, field bytes, x bytes)
     "df64": (1152, 48, 48)}
 
 
-def _k1_k2_bytes(inner):
+def _k1_k2_bytes(inner, folded=False):
+    """(K1, K2) algorithmic bytes per output site. `folded`: the FP32 recursion's K1 forms
+    p = r + beta p_old itself, so it reads r and p_old and writes p and ap (no separate p kernel)."""
     link_b, fld_b, x_b = OP_BYTES[inner]
-    return link_b + 2 * fld_b, link_b + fld_b + 2 * fld_b + x_b + fld_b + x_b
+    k1 = link_b + 4 * fld_b if folded else link_b + 2 * fld_b
+    return k1, link_b + fld_b + 2 * fld_b + x_b + fld_b + x_b
 
 
 def _measured_peaks():
@@ -565,7 +568,7 @@ def run_gpu_mixed32(args, wl):
 
     # ---- the other recursions on the same lattice and source
     legs, sols = {}, {head: x_mixed}
-    for inner in ("double", "half12", "df64"):
+    for inner in (() if args.no_legs else ("double", "half12", "df64")):
         if inner == "df64" and args.no_variant:
             continue
         step(inner)
@@ -576,14 +579,15 @@ def run_gpu_mixed32(args, wl):
                        "value": round(flops_of(inf_l) / (sum(ms_l) * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
                        "iterations": i["iterations"], "reliable_updates": i["reliable_updates"],
                        "true_rel_residual": i["true_rel_residual"]}
-    t_fp64 = legs["double"]["ms_per_step"]
+    t_fp64 = legs["double"]["ms_per_step"] if legs else None
 
     # ---- accuracy of every solution: oracle residual at sampled sites, distance to the FP64 solution
-    x64 = sols["double"]
+    x64 = sols.get("double")
     accuracy = {}
     for inner, xs in sols.items():
-        accuracy[inner] = {"oracle_rel_residual_2000_even_sites": sampled_oracle_residual(U, xs, b, dims, mass),
-                           "rel_diff_vs_plain_fp64_gpu_solution": float(np.linalg.norm(xs - x64) / np.linalg.norm(x64))}
+        accuracy[inner] = {"oracle_rel_residual_2000_even_sites": sampled_oracle_residual(U, xs, b, dims, mass)}
+        if x64 is not None:
+            accuracy[inner]["rel_diff_vs_plain_fp64_gpu_solution"] = float(np.linalg.norm(xs - x64) / np.linalg.norm(x64))
 
     # ---- the half-lattice operator alone, per precision: back-to-back qcd_dslash launches that
     # alternate between two lattices with their own links (so that the links stream from DRAM even
@@ -591,9 +595,9 @@ def run_gpu_mixed32(args, wl):
     lat2 = Q.Lattice(dims)
     bufs2 = {p: lat2.empty_bytes(Q.qcd_links_bytes(lat2.handle, p, r)) for p, r in pack_of.values()}
     operators = {}
-    fp64_meas = fp64_gemm_tflops()
+    fp64_meas = None if args.no_legs else fp64_gemm_tflops()
     n_op = 40
-    for name, (p, r) in pack_of.items():
+    for name, (p, r) in (() if args.no_legs else pack_of.items()):
         with torch.cuda.stream(stream):
             for L_, B_ in ((lat, bufs), (lat2, bufs2)):
                 Q.qcd_load_links(L_.handle, U_dev, B_[p], p, r, stream)
@@ -636,7 +640,7 @@ def run_gpu_mixed32(args, wl):
     n32 = 2 * i["iterations"]
     n_all = _half_dslash_count(i)
     n64 = n_all - n32
-    k1_32, k2_32 = _k1_k2_bytes(head)
+    k1_32, k2_32 = _k1_k2_bytes(head, folded=True)
     k1_64, k2_64 = _k1_k2_bytes("double")
     alg_step = Vh * (i["iterations"] * (k1_32 + k2_32) + n64 / 2 * (k1_64 + k2_64))
     per_launch_us = t_mixed * 1e3 / n_all
@@ -648,7 +652,8 @@ def run_gpu_mixed32(args, wl):
         "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
         "traffic": ncu_traffic(args.workload),
         "method": "all of the timed step's time charged to its operator launches (a lower bound on the "
-                  "kernels' rate); per-launch bytes = the mean of K1 and K2 at the launch's precision",
+                  "kernels' rate); per-launch bytes = the mean of K1 and K2 at the launch's precision (the FP32 "
+                  "K1 also forms p = r + beta p: links + r + p_old + p + ap)",
         "alg_bytes_per_site_k1_k2": [k1_32, k2_32], "alg_bytes_per_site_k1_k2_fp64": [k1_64, k2_64],
         "alg_bytes_per_step": round(alg_step), "alg_bytes_per_launch_fp32": (k1_32 + k2_32) / 2 * Vh,
         "check": {"operator_launches": n_all, "fp32_launches": n32, "fp64_launches": n64,
@@ -662,7 +667,7 @@ def run_gpu_mixed32(args, wl):
 
     # ---- config 4: the multi-RHS and many-lattice solves (their own lattices and sources)
     batched = {}
-    if not args.no_batched:
+    if not args.no_batched and not args.no_legs:
         for key in ("mrhs24_single12", "batch64_single12"):
             bl = batched_leg(WORKLOADS[key], leg_steps if key.startswith("mrhs") else max(leg_steps, 5), 1, False,
                              key, world, local, fp64_steps=max(1, min(leg_steps, 2)), sample_clocks=False)
@@ -682,13 +687,14 @@ def run_gpu_mixed32(args, wl):
         "cg": {"iterations": i["iterations"], "true_rel_residual": i["true_rel_residual"],
                "reliable_updates": i["reliable_updates"], "time_to_solution_ms": round(t_mixed, 4),
                "half_dslash_per_solve": n_all, "plain_fp64_ms": t_fp64,
-               "speedup_vs_fp64": round(t_fp64 / t_mixed, 3),
-               "speedup_vs_fp64_half12": round(t_fp64 / legs["half12"]["ms_per_step"], 3)},
+               "speedup_vs_fp64": round(t_fp64 / t_mixed, 3) if t_fp64 else None,
+               "speedup_vs_fp64_half12": round(t_fp64 / legs["half12"]["ms_per_step"], 3) if t_fp64 else None},
         "legs": legs,
         "accuracy": accuracy,
         "roofline": roofline,
         "operators": operators,
-        "fp64_peak": {"derived_tflops": round(FP64_PEAK_TFLOPS, 4), "measured_dgemm_tflops": round(fp64_meas, 4),
+        "fp64_peak": {"derived_tflops": round(FP64_PEAK_TFLOPS, 4),
+                      "measured_dgemm_tflops": round(fp64_meas, 4) if fp64_meas else None,
                       "note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; measured: cuBLAS DGEMM 4096^3 "
                               "(torch.matmul float64), best of 3"},
         "batched": batched,
@@ -1654,6 +1660,9 @@ def main():
     ap.add_argument("--leg-steps", type=int, default=3,
                     help="timed steps of each side measurement of the cg32_mixed workload (after one untimed)")
     ap.add_argument("--no-batched", action="store_true", help="cg32_mixed: skip the batched solves")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="cg32_mixed: the headline solve only (no other precisions, operators or batched solves; "
+                         "for counter captures)")
     ap.add_argument("--reliable-delta", type=float, default=None,
                     help="mixed Wilson CGNR: reliable-update threshold (default: the workload's, else the library's)")
     args = ap.parse_args()

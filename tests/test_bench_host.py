@@ -69,6 +69,8 @@ def test_k1_k2_bytes_match_the_per_site_table():
     assert bench._k1_k2_bytes("double") == (1248, 1440)
     assert bench._k1_k2_bytes("single12") == (432, 528)
     assert bench._k1_k2_bytes("half12") == (224, 304)
+    # the FP32 K1 with p = r + beta p folded in: links + r + p_old read + p + ap written
+    assert bench._k1_k2_bytes("single12", folded=True) == (480, 528)
 
 
 def test_oracle_pool_applies_a_over_every_even_site_on_several_processes():
