@@ -81,8 +81,12 @@ typedef struct {
   int use_graph;         /* replay each k-iteration chunk as a CUDA graph (1)                     */
   int profile;           /* record CUDA events around every operator launch of the iteration (0);
                             profiled chunks run as direct launches, not graph replays         */
-  int rhs_block;         /* multi-RHS solves: right-hand sides per register block, 1/2/4/8/16;
-                            0 = the tuned value if qcd_tune_mrhs recorded one, else a default   */
+  int rhs_block;         /* staggered multi-RHS solves: right-hand sides per register block,
+                            1/2/4/8/16; -1 = the shared-link kernel (a block loads each link of
+                            its tile once into shared memory and applies it to every RHS);
+                            0 = the tuned value if qcd_tune_mrhs recorded one, else -1 from 8
+                            RHS on and a register block below. Wilson multi-RHS: see
+                            qcd_wilson_cgnr_mrhs                                                */
   int cluster_size;      /* batched solves: thread blocks per cluster (one cluster per lattice
                             at a time), 1/2/4/8/16; 0 = tuned value or 4                        */
   int block_size;        /* batched solves: threads per block, multiple of 32 <= 256; 0 = tuned
@@ -351,8 +355,9 @@ QCD_API int qcd_wilson_cgnr_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const 
 /* ---- autotuning of launch shapes (no counterpart in the paper) ------------------------------ */
 
 /* Time the multi-RHS solver's operator launches (CUDA events over a 24-iteration run of the real
- * solve on the caller's buffers, the same arguments as qcd_cg_solve_mrhs) for each register block
- * of right-hand sides, store the fastest in the in-process table used when opts->rhs_block == 0,
+ * solve on the caller's buffers, the same arguments as qcd_cg_solve_mrhs) for the shared-link
+ * kernel (-1, from 2 RHS on) and each register block of right-hand sides, store the fastest in the
+ * in-process table used when opts->rhs_block == 0,
  * append it to `cache_path` (nullable) and return it in *best_rhs_block. x_dev is overwritten. */
 QCD_API int qcd_tune_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, double mass,
                   const qcd_solver_opts* opts, void* workspace_dev, const char* cache_path, int* best_rhs_block,

@@ -354,9 +354,9 @@ static int check_solve_args(const qcd_lattice* lat, void* x_dev, const void* b_d
   if (opts) o = *opts;
   if (!valid_prec(o.prec_inner)) return invalid("unknown inner precision %d", o.prec_inner);
   if (o.reliable_delta < 0.0 || o.reliable_delta >= 1.0) return invalid("reliable_delta must be in [0, 1)");
-  if (o.rhs_block != 0 && o.rhs_block != 1 && o.rhs_block != 2 && o.rhs_block != 4 && o.rhs_block != 8 &&
-      o.rhs_block != 16)
-    return invalid("rhs_block must be 0, 1, 2, 4, 8 or 16, got %d", o.rhs_block);
+  if (o.rhs_block != -1 && o.rhs_block != 0 && o.rhs_block != 1 && o.rhs_block != 2 && o.rhs_block != 4 &&
+      o.rhs_block != 8 && o.rhs_block != 16)
+    return invalid("rhs_block must be -1, 0, 1, 2, 4, 8 or 16, got %d", o.rhs_block);
   if (int rc = check_links(lat, QCD_PREC_DOUBLE)) return rc;
   if (int rc = check_links(lat, o.prec_inner)) return rc;
   if (o.prec_inner != QCD_PREC_DOUBLE && lat->links[o.prec_inner].recon != o.recon_inner) {

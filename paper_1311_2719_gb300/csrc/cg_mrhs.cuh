@@ -129,6 +129,116 @@ __global__ void __launch_bounds__(kBlock, MrhsMinBlocks<LinksT, RB>::value) dsla
   }
 }
 
+// ---------------------------------------------------------------- operator kernel with shared links
+// For many right-hand sides: a block of kShWarps warps takes a tile of kShTile consecutive output
+// sites. In the load phase warp w fetches link slot w of the tile's sites (direction w / 2, forward or
+// backward; one lane per site, coalesced), rebuilds the third row of a compressed link, applies
+// 1/2 eta zeta where the format does not fold it in, turns a backward link into -U^dagger, and stores
+// the result in shared memory. After a barrier, warp w applies the eight stored links of each site
+// to right-hand sides w and w + kShWarps. Every link is read from memory once per launch; the grid
+// rows of dslash_mrhs_cg_kernel instead re-read it from L2 once per RHS block (at 24^4 x 16 RHS, 1 GB
+// of L2 reads per launch against 64 MB of links).
+constexpr int kShTile = 32;
+constexpr int kShWarps = 8;
+constexpr int kShThreads = kShTile * kShWarps;
+constexpr int kRhsShared = -1;  // the rhs_block option value that selects this kernel
+static_assert(2 * kShWarps >= kMaxRhs, "two right-hand sides per warp cover every RHS");
+
+// resident blocks per SM: 4 (64 registers, 32 warps to hide the neighbour gathers) in FP32 arithmetic;
+// 2 for the 64-bit types, which spill below 128 registers
+template <class LinksT>
+struct ShMinBlocks {
+  static constexpr int value = sizeof(typename LinksT::T) == 4 ? 4 : 2;
+};
+
+template <class LinksT, class FieldT, class Epi>
+__global__ void __launch_bounds__(kShThreads, ShMinBlocks<LinksT>::value) dslash_mrhs_shared_kernel(Geom g, LinksT U, FieldT in, int nrhs,
+                                                                          int out_par, Epi epi) {
+  using T = typename LinksT::T;
+  using A = typename Accum<T>::type;
+  __shared__ __align__(16) unsigned char sl_raw[kShWarps * 9 * kShTile * sizeof(cplx<T>)];
+  cplx<T>* sl = reinterpret_cast<cplx<T>*>(sl_raw);  // [slot][element][site of the tile]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned run = 0;
+  for (int q = 0; q < nrhs; ++q)
+    if (epi.sc[q].done == kRunning) run |= 1u << q;
+  if (!run) return;  // every block reads the same flags: none of them arrives below
+  const int q0 = w, q1 = w + kShWarps;
+  const bool act0 = q0 < nrhs && ((run >> q0) & 1u), act1 = q1 < nrhs && ((run >> q1) & 1u);
+  A part0 = A(0), part1 = A(0);
+  const int mu = w >> 1, back = w & 1;
+  const int ntiles = (g.Vh + kShTile - 1) / kShTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int k = tile * kShTile + lane;
+    const bool valid = k < g.Vh;
+    Site s{};
+    int fwd[4] = {0, 0, 0, 0}, bwd[4] = {0, 0, 0, 0};
+    if (valid) {
+      s = site_of(g, k, out_par);
+      neighbours(g, s, fwd, bwd);
+      su3<T> L;
+      if (!back) {
+        L = U.load(out_par, mu, k);
+        if constexpr (!LinksT::kFolded) scale(L, T(0.5f * fwd_sign(g, s, mu)));
+      } else {
+        const su3<T> B = U.load(1 - out_par, mu, bwd[mu]);
+        const T c = LinksT::kFolded ? T(-1.0f) : T(-0.5f * bwd_sign(g, s, mu));  // c U^dagger
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            L.e[a][b].re = c * B.e[b][a].re;
+            L.e[a][b].im = -(c * B.e[b][a].im);
+          }
+      }
+#pragma unroll
+      for (int e = 0; e < 9; ++e) sl[(w * 9 + e) * kShTile + lane] = L.e[e / 3][e % 3];
+    }
+    __syncthreads();
+    if (valid && (act0 || act1)) {
+      cvec3<T> acc0, acc1;
+      zero(acc0);
+      zero(acc1);
+      const FieldT in0 = field_at(in, act0 ? q0 : 0), in1 = field_at(in, act1 ? q1 : 0);
+#pragma unroll
+      for (int slot = 0; slot < kShWarps; ++slot) {
+        const int nb = (slot & 1) ? bwd[slot >> 1] : fwd[slot >> 1];
+        su3<T> M;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) M.e[e / 3][e % 3] = sl[(slot * 9 + e) * kShTile + lane];
+        if (act0) mul_add(acc0, M, in0.load(nb));
+        if (act1) mul_add(acc1, M, in1.load(nb));
+      }
+      if (act0) epi.site(k, q0, acc0, part0);
+      if (act1) epi.site(k, q1, acc1, part1);
+    }
+    __syncthreads();  // the slots are refilled by the next tile
+  }
+  // This block's partial for RHS q is warp (q mod kShWarps)'s sum; its writer fences before the
+  // barrier, and thread 0 arrives for the block.
+  __shared__ bool am_last;
+  {
+    const double v0 = warp_sum((double)part0), v1 = warp_sum((double)part1);
+    if (lane == 0) {
+      if (q0 < nrhs) epi.partials[(size_t)q0 * kMaxPartials + blockIdx.x] = v0;
+      if (q1 < nrhs) epi.partials[(size_t)q1 * kMaxPartials + blockIdx.x] = v1;
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(&epi.sc[0].counter[Epi::kCounter], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (am_last) {
+    __shared__ double tot[kMaxRhs];
+    mrhs_totals(nrhs, epi.partials, tot);
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < nrhs; ++q)
+        if (epi.sc[q].done == kRunning) epi.update(q, tot[q]);
+      epi.sc[0].counter[Epi::kCounter] = 0u;
+    }
+  }
+}
+
 // K1: ap_r = D_oe p_r, alpha_r = rr_r / (|ap_r|^2 + m^2 |p_r|^2)
 template <class FieldT>
 struct EpiApM {
@@ -240,6 +350,26 @@ struct MrhsRunner {
     if (ev) cudaEventRecord(ev[3], st);
   }
 
+  // The shared-link kernel: one wave of its blocks (at most one per tile).
+  void launch_shared(const Links<PREC, RECON>& U, FieldT p, FieldT ap, FieldT r, XFieldT x, cudaEvent_t* ev) {
+    auto k2 = dslash_mrhs_shared_kernel<Links<PREC, RECON>, FieldT, EpiUpdateM<FieldT, XFieldT>>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2, kShThreads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    long long gx = (long long)sms * per_sm;
+    const long long tiles = (g.Vh + kShTile - 1) / kShTile;
+    if (gx > tiles) gx = tiles;
+    if (gx > kMaxPartials) gx = kMaxPartials;
+    if (ev) cudaEventRecord(ev[0], st);
+    dslash_mrhs_shared_kernel<Links<PREC, RECON>, FieldT><<<(int)gx, kShThreads, 0, st>>>(
+        g, U, p, R, QCD_ODD, EpiApM<FieldT>{ap, w.sc, w.partials});
+    if (ev) cudaEventRecord(ev[1], st);
+    if (ev) cudaEventRecord(ev[2], st);
+    k2<<<(int)gx, kShThreads, 0, st>>>(g, U, ap, R, QCD_EVEN, EpiUpdateM<FieldT, XFieldT>{p, r, x, w.sc, w.partials});
+    if (ev) cudaEventRecord(ev[3], st);
+  }
+
   int iteration(cudaEvent_t* ev = nullptr) {
     auto U = make_links<PREC, RECON>(lat->links[PREC].ptr, g.Vh);
     FieldT r = make_field<PREC>(w.r, g.Vh), p = make_field<PREC>(w.p, g.Vh), ap = make_field<PREC>(w.ap, g.Vh);
@@ -247,6 +377,7 @@ struct MrhsRunner {
     cg_p_mrhs_kernel<<<dim3(wave_x(cg_p_mrhs_kernel<FieldT>, R), R), kBlock, 0, st>>>(g.Vh, r, p, R, w.sc, w.partials);
     constexpr bool wide = PREC == QCD_PREC_DOUBLE || PREC == QCD_PREC_DF64;  // 64-bit accumulators: RB <= 4
     switch (rb) {
+      case kRhsShared: launch_shared(U, p, ap, r, x, ev); break;
       case 1: launch_ops<1>(U, p, ap, r, x, ev); break;
       case 2: launch_ops<2>(U, p, ap, r, x, ev); break;
       case 4: launch_ops<4>(U, p, ap, r, x, ev); break;
@@ -270,7 +401,8 @@ struct MrhsRunner {
   }
 };
 
-// Default RHS block (when nothing is tuned). Links that fit in half of L2 are read from L2 by
+// Default RHS block (when nothing is tuned): the shared-link kernel from kShWarps right-hand sides
+// on (fewer leave warps of its blocks idle). Links that fit in half of L2 are read from L2 by
 // every grid row, so register blocking buys nothing and costs registers: 1 (measured on GB300 at
 // 24^4 x 16 RHS, FP32 recon-12, links 64 MB: 276 ms per solve against 303 ms with 4). Larger link
 // fields would be streamed from DRAM once per row: up to 4 RHS per row. (16 RHS in registers take
@@ -278,6 +410,7 @@ struct MrhsRunner {
 // 8 or 16 where they pay.)
 inline int default_rhs_block(int prec, int R, size_t links_bytes) {
   (void)prec;
+  if (R >= kShWarps) return kRhsShared;
   int dev = 0, l2 = 0;
   if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
       l2 > 0 && links_bytes * 2 <= (size_t)l2)

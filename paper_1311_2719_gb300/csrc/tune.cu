@@ -113,12 +113,13 @@ int qcd_tune_mrhs(qcd_lattice* lat, int nrhs, void* x_dev, const void* b_dev, do
   qcd_solver_opts o;
   if (int rc = check_mrhs_args(lat, nrhs, x_dev, b_dev, nullptr, mass, 1e-14, 24, opts, workspace_dev, o)) return rc;
   o.profile = 1;
-  const int cands[] = {1, 2, 4, 8, 16};
+  const int cands[] = {-1, 1, 2, 4, 8, 16};  // -1: the shared-link kernel
   double best_us = 1e300;
   int best = 0;
   std::vector<qcd_solve_info> info(nrhs);
   for (int rb : cands) {
     if (rb > 2 * nrhs && rb > 1) break;
+    if (rb == -1 && nrhs < 2) continue;
     if ((o.prec_inner == QCD_PREC_DOUBLE || o.prec_inner == QCD_PREC_DF64) && rb > 4) break;  // 64-bit accumulators
     o.rhs_block = rb;
     // a short run of the real solve (it stops at max_iter; only the launch timings matter)

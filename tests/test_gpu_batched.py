@@ -57,6 +57,26 @@ def test_mrhs_cg_matches_oracle(H, inner, nrhs):
         assert H.rel(y[r], S.dslash_parity(U, x[r], dims, 1)) <= 1e-12
 
 
+@pytest.mark.parametrize("inner", ["double", "single12", "half12", "df64"])
+@pytest.mark.parametrize("dims,nrhs", [((6, 4, 4, 8), 3), ((10, 4, 6, 8), 9), ((8, 8, 8, 8), 16)])
+def test_mrhs_shared_link_kernel_matches_oracle(H, inner, dims, nrhs):
+    """The shared-link multi-RHS operator (rhs_block = -1): tiles of 32 sites with a ragged last
+    tile (10x4x6x8: 960 sites per parity), fewer RHS than warps, one and two RHS per warp."""
+    m = 0.1
+    U = I.make_links(dims, kind="haar", seed=1)
+    bs = list(I.make_sources(dims, nrhs, first_seed=2))
+    rig = H.Rig(dims, U, precs=sorted({"double", inner}))
+    rc, infos, x, y = _mrhs(H, rig, bs, m, inner, rb=-1)
+    assert rc == Q.QCD_OK, infos
+    for r in range(nrhs):
+        assert infos[r]["converged"] and infos[r]["true_rel_residual"] <= 1e-10
+        assert S.true_residual(U, x[r], bs[r], dims, m) <= 1.01e-10
+        assert H.rel(y[r], S.dslash_parity(U, x[r], dims, 1)) <= 1e-12
+    for r in (0, nrhs - 1):
+        ref = S.cg_solve(U, bs[r], dims, m, tol=1e-12, max_iter=5000)
+        assert H.rel(x[r], ref["x"]) <= _kappa(m) * 1e-10
+
+
 def test_mrhs_fp64_agrees_with_single_rhs_solves(H):
     """The multi-RHS FP64 solve follows the single-RHS recursion (the single-RHS operator splits a
     small lattice's hops over lane pairs, so the rounding order differs slightly)."""
@@ -81,7 +101,7 @@ def test_mrhs_results_agree_across_rhs_blocks(H):
     U = I.make_links(dims, kind="haar", seed=3)
     bs = list(I.make_sources(dims, 5, first_seed=7))
     rig = H.Rig(dims, U, precs=["double", "single12"])
-    outs = [_mrhs(H, rig, bs, m, "single12", rb=rb)[2] for rb in (1, 2, 4, 8, 16)]
+    outs = [_mrhs(H, rig, bs, m, "single12", rb=rb)[2] for rb in (1, 2, 4, 8, 16, -1)]
     for o in outs[1:]:
         for r in range(5):
             assert H.rel(o[r], outs[0][r]) <= _kappa(m) * 2e-10
