@@ -731,7 +731,8 @@ def run_gpu_batched(args, wl):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    out = batched_leg(wl, args.steps, args.warmup, args.tune, args.workload, world, local)
+    out = batched_leg(wl, args.steps, args.warmup, args.tune, args.workload, world, local,
+                      fp64_steps=0 if args.no_legs else 3)
     if world > 1:
         dist.destroy_process_group()
     return out if rank == 0 else None
@@ -855,14 +856,16 @@ def batched_leg(wl, steps, warmup, tune, workload_key, world=1, local=0, fp64_st
                     if rc != Q.QCD_OK:
                         raise RuntimeError("FP64 reference solve failed")
         return 0
-    fp64_step()
-    ms64, _ = timed(fp64_step, max(1, fp64_steps))
+    ms64 = []
+    if fp64_steps > 0:
+        fp64_step()
+        ms64, _ = timed(fp64_step, fp64_steps)
 
     (t_all,), (fl_all,) = reduce_over_ranks([sum(ms)], [sum(o[0] for o in outs)])
     value = fl_all / (t_all * 1e-3) / 1e9
     infos = outs[-1][1]
     t_batched = sum(ms) / steps
-    t_fp64 = sum(ms64) / len(ms64)
+    t_fp64 = sum(ms64) / len(ms64) if ms64 else None
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": round(t_batched, 4), "higher_is_better": True, "scaling": "weak",
@@ -876,8 +879,8 @@ def batched_leg(wl, steps, warmup, tune, workload_key, world=1, local=0, fp64_st
                "max_iterations": max(i["iterations"] for i in infos),
                "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
                "reliable_updates": sum(i["reliable_updates"] for i in infos),
-               "plain_fp64_gpu_cg_ms": round(t_fp64, 4), "plain_fp64_steps": len(ms64),
-               "speedup_vs_plain_fp64_gpu_cg": round(t_fp64 / t_batched, 3)},
+               "plain_fp64_gpu_cg_ms": round(t_fp64, 4) if t_fp64 else None, "plain_fp64_steps": len(ms64),
+               "speedup_vs_plain_fp64_gpu_cg": round(t_fp64 / t_batched, 3) if t_fp64 else None},
         "gpu_launches": int(sum(o[2] for o in outs)),
         "clocks": clocks,
         "tuned": tuned,
@@ -1664,8 +1667,8 @@ def main():
                     help="timed steps of each side measurement of the cg32_mixed workload (after one untimed)")
     ap.add_argument("--no-batched", action="store_true", help="cg32_mixed: skip the batched solves")
     ap.add_argument("--no-legs", action="store_true",
-                    help="cg32_mixed: the headline solve only (no other precisions, operators or batched solves; "
-                         "for counter captures)")
+                    help="the headline solve only (cg32_mixed: no other precisions, operators or batched solves; "
+                         "batched workloads: no one-by-one FP64 comparison), for counter captures")
     ap.add_argument("--reliable-delta", type=float, default=None,
                     help="mixed Wilson CGNR: reliable-update threshold (default: the workload's, else the library's)")
     args = ap.parse_args()

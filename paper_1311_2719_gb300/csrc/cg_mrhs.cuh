@@ -60,11 +60,9 @@ __global__ void __launch_bounds__(kBlock) cg_p_mrhs_kernel(int Vh, FieldT r_all,
   if (mrhs_arrive<1>(red, r, nrhs, partials, &sc[0].counter[kCtrK3M])) {
     __shared__ double tot[kMaxRhs];
     mrhs_totals(nrhs, partials, tot);
-    if (threadIdx.x == 0) {
-      for (int q = 0; q < nrhs; ++q)
-        if (sc[q].done == kRunning) sc[q].pp = tot[q];
-      sc[0].counter[kCtrK3M] = 0u;
-    }
+    // one thread per right-hand side (each update is a chain of dependent global loads and stores)
+    if (threadIdx.x < nrhs && sc[threadIdx.x].done == kRunning) sc[threadIdx.x].pp = tot[threadIdx.x];
+    if (threadIdx.x == 0) sc[0].counter[kCtrK3M] = 0u;
   }
 }
 
@@ -121,11 +119,10 @@ __global__ void __launch_bounds__(kBlock, MrhsMinBlocks<LinksT, RB>::value) dsla
   if (mrhs_arrive<RB>(red, r0, nrhs, epi.partials, &epi.sc[0].counter[Epi::kCounter])) {
     __shared__ double tot[kMaxRhs];
     mrhs_totals(nrhs, epi.partials, tot);
-    if (threadIdx.x == 0) {
-      for (int q = 0; q < nrhs; ++q)
-        if (epi.sc[q].done == kRunning) epi.update(q, tot[q]);
-      epi.sc[0].counter[Epi::kCounter] = 0u;
-    }
+    // one thread per right-hand side: a serial loop over sixteen updates (dependent global loads and
+    // stores, an FP64 division each) kept the summing block's SM busy ~70k cycles after the others
+    if (threadIdx.x < nrhs && epi.sc[threadIdx.x].done == kRunning) epi.update(threadIdx.x, tot[threadIdx.x]);
+    if (threadIdx.x == 0) epi.sc[0].counter[Epi::kCounter] = 0u;
   }
 }
 
@@ -231,11 +228,10 @@ __global__ void __launch_bounds__(kShThreads, ShMinBlocks<LinksT>::value) dslash
   if (am_last) {
     __shared__ double tot[kMaxRhs];
     mrhs_totals(nrhs, epi.partials, tot);
-    if (threadIdx.x == 0) {
-      for (int q = 0; q < nrhs; ++q)
-        if (epi.sc[q].done == kRunning) epi.update(q, tot[q]);
-      epi.sc[0].counter[Epi::kCounter] = 0u;
-    }
+    // one thread per right-hand side: a serial loop over sixteen updates (dependent global loads and
+    // stores, an FP64 division each) kept the summing block's SM busy ~70k cycles after the others
+    if (threadIdx.x < nrhs && epi.sc[threadIdx.x].done == kRunning) epi.update(threadIdx.x, tot[threadIdx.x]);
+    if (threadIdx.x == 0) epi.sc[0].counter[Epi::kCounter] = 0u;
   }
 }
 

@@ -427,11 +427,9 @@ __global__ void __launch_bounds__(kBlock, WMrhsMinBlocks<typename LinksT::T, RB>
     if (am_last) {
       __shared__ double tot[kMaxRhs];
       mrhs_totals(nrhs, epi.partials, tot);
-      if (threadIdx.x == 0) {
-        for (int q = 0; q < nrhs; ++q)
-          if (epi.running(q)) epi.update(q, tot[q]);
-        *epi.counter() = 0u;
-      }
+      // one thread per right-hand side (each update is a chain of dependent global loads and stores)
+      if (threadIdx.x < nrhs && epi.running(threadIdx.x)) epi.update(threadIdx.x, tot[threadIdx.x]);
+      if (threadIdx.x == 0) *epi.counter() = 0u;
     }
   }
 }
