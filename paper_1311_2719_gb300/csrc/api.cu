@@ -657,8 +657,9 @@ static int wilson_cgnr_common(qcd_lattice* lat, int nrhs, void* x_dev, const voi
   if (o.prec_outer != QCD_PREC_DOUBLE && !(o.prec_outer == QCD_PREC_DF64 && o.prec_inner == QCD_PREC_SINGLE))
     return done(invalid("Wilson CGNR: outer precision must be DOUBLE, or DF64 with a SINGLE inner precision"));
   if (o.reliable_delta < 0.0 || o.reliable_delta >= 1.0) return done(invalid("reliable_delta must be in [0, 1)"));
-  if (wilson_rhs_block(o.prec_inner, nrhs, o.rhs_block) < 1)
-    return done(invalid("rhs_block %d is not supported for Wilson precision %d (1, 2 or 4 for SINGLE; 1 or 2 for DOUBLE)",
+  if (wilson_rhs_block(o.prec_inner, nrhs, o.rhs_block) == 0)
+    return done(invalid("rhs_block %d is not supported for Wilson precision %d (-1 for the shared-link kernel; 1, 2 "
+                        "or 4 for SINGLE; 1 or 2 for DOUBLE)",
                         o.rhs_block, o.prec_inner));
   if (!lat->wilson_links[o.prec_outer] || !lat->wilson_links[o.prec_inner]) {
     set_error("Wilson links must be loaded at the outer and at the inner precision");

@@ -135,11 +135,6 @@ __global__ void __launch_bounds__(kBlock, MrhsMinBlocks<LinksT, RB>::value) dsla
 // to right-hand sides w and w + kShWarps. Every link is read from memory once per launch; the grid
 // rows of dslash_mrhs_cg_kernel instead re-read it from L2 once per RHS block (at 24^4 x 16 RHS, 1 GB
 // of L2 reads per launch against 64 MB of links).
-constexpr int kShTile = 32;
-constexpr int kShWarps = 8;
-constexpr int kShThreads = kShTile * kShWarps;
-constexpr int kRhsShared = -1;  // the rhs_block option value that selects this kernel
-static_assert(2 * kShWarps >= kMaxRhs, "two right-hand sides per warp cover every RHS");
 
 // resident blocks per SM: 4 (64 registers, 32 warps to hide the neighbour gathers) in FP32 arithmetic;
 // 2 for the 64-bit types, which spill below 128 registers

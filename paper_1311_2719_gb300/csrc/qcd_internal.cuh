@@ -16,6 +16,12 @@ constexpr int kBlock = 128;           // threads per block of the site kernels
 constexpr int kSpreadBlockMax = 512;  // widest block of the CG kernels on lattices below one wave
 constexpr int kMaxPartials = 8192;    // per-reduction partial slots in the workspace
 constexpr int kMaxRhs = 16;
+// shared-link multi-RHS operators (staggered and Wilson): tiles of kShTile sites, kShWarps warps
+constexpr int kShTile = 32;
+constexpr int kShWarps = 8;
+constexpr int kShThreads = kShTile * kShWarps;
+constexpr int kRhsShared = -1;  // the rhs_block option value that selects them
+static_assert(2 * kShWarps >= kMaxRhs, "two right-hand sides per warp cover every RHS");
 
 // ------------------------------------------------------------------------------------------
 // Host-side handle.

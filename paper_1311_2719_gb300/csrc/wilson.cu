@@ -434,6 +434,103 @@ __global__ void __launch_bounds__(kBlock, WMrhsMinBlocks<typename LinksT::T, RB>
   }
 }
 
+// ---------------------------------------------------------------- multi-RHS operator with shared links
+// A block of kShWarps warps takes a tile of kShTile consecutive sites. Warp w loads link slot w of the
+// tile (direction w / 2: the forward link U_mu(i) or the backward link U_mu(i - mu)) once, one lane
+// per site, into shared memory; after a barrier warp w applies the tile's eight links to right-hand
+// sides w and w + kShWarps (through the two-row spin projection, the link read back from shared
+// memory for each RHS). Every link is read from memory once per launch; dslash-style register
+// blocking instead reloads the links for every block of RHS (measured at 32^3 x 64 x 8 RHS: K1 moved
+// 1.6 times its algorithmic bytes).
+template <typename T>
+struct WShMinBlocks {  // 256-thread blocks per SM: 2 (128 registers) for FP32, 1 for 64-bit types
+  static constexpr int value = sizeof(T) == 4 ? 2 : 1;
+};
+
+template <class LinksT, class FieldT, bool G5IN, class Epi>
+__global__ void __launch_bounds__(kShThreads, WShMinBlocks<typename LinksT::T>::value)
+    wilson_mrhs_shared_kernel(Geom g, int V, LinksT U, FieldT in, int nrhs, Epi epi) {
+  using T = typename LinksT::T;
+  using A = typename Accum<T>::type;
+  __shared__ __align__(16) unsigned char sl_raw[kShWarps * 9 * kShTile * sizeof(cplx<T>)];
+  cplx<T>* sl = reinterpret_cast<cplx<T>*>(sl_raw);  // [slot][element][site of the tile]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned run = 0;
+  for (int q = 0; q < nrhs; ++q)
+    if (epi.running(q)) run |= 1u << q;
+  if (!run) return;  // every block reads the same flags: none of them arrives below
+  A part[2] = {A(0), A(0)};
+  const int ntiles = (V + kShTile - 1) / kShTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i = tile * kShTile + lane;
+    const bool valid = i < V;
+    int c[4] = {0, 0, 0, 0};
+    if (valid) {
+      full_site(g, i, c);
+      const int mu = w >> 1, dir = w & 1;
+      const su3<T> L = U.load(mu, dir == 0 ? i : w_neighbour(g, i, c, mu, 1));
+#pragma unroll
+      for (int e = 0; e < 9; ++e) sl[(w * 9 + e) * kShTile + lane] = L.e[e / 3][e % 3];
+    }
+    __syncthreads();
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int q = w + j * kShWarps;
+        if (q >= nrhs || !((run >> q) & 1u)) continue;
+        spinor<T> acc;
+        zero(acc);
+#pragma unroll
+        for (int slot = 0; slot < kShWarps; ++slot) {
+          const int mu = slot >> 1, dir = slot & 1;
+          su3<T> Ul;
+#pragma unroll
+          for (int e = 0; e < 9; ++e) Ul.e[e / 3][e % 3] = sl[(slot * 9 + e) * kShTile + lane];
+          hop_accumulate<G5IN>(acc, Ul, in.at(q).load(w_neighbour(g, i, c, mu, dir)), mu, dir);
+        }
+        A pt = A(0);
+        epi.site(i, q, acc, pt);
+        part[j] += pt;
+      }
+    }
+    __syncthreads();  // the slots are refilled by the next tile
+  }
+  if constexpr (Epi::kReduce) {
+    // the block's partial for RHS q is warp (q mod kShWarps)'s sum; its writer fences before the
+    // barrier, thread 0 arrives for the block
+    __shared__ bool am_last;
+    const double v0 = warp_sum((double)part[0]), v1 = warp_sum((double)part[1]);
+    if (lane == 0) {
+      if (w < nrhs) epi.partials[(size_t)w * kMaxPartials + blockIdx.x] = v0;
+      if (w + kShWarps < nrhs) epi.partials[(size_t)(w + kShWarps) * kMaxPartials + blockIdx.x] = v1;
+      __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = atomicAdd(epi.counter(), 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (am_last) {
+      __shared__ double tot[kMaxRhs];
+      mrhs_totals(nrhs, epi.partials, tot);
+      if (threadIdx.x < nrhs && epi.running(threadIdx.x)) epi.update(threadIdx.x, tot[threadIdx.x]);
+      if (threadIdx.x == 0) *epi.counter() = 0u;
+    }
+  }
+}
+
+// one wave of the shared-link kernel's blocks (at most one per tile)
+template <class KernelT>
+static int w_shared_grid(KernelT kernel, int V) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kShThreads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  long long gx = (long long)sms * per_sm;
+  const long long tiles = (V + kShTile - 1) / kShTile;
+  if (gx > tiles) gx = tiles;
+  if (gx > kMaxPartials) gx = kMaxPartials;
+  return (int)gx;
+}
+
 // counter slots of sc[0] used by the multi-RHS CGNR kernels (the FP64 residual epilogue uses slot 4 of sc[r])
 enum { kCtrWT = 9, kCtrWU = 10 };
 
@@ -887,12 +984,15 @@ static dim3 w_grid(KernelT kernel, long long V, int gy) {
 }
 
 // register block of right-hand sides: the opts value if given (1, 2, 4 in FP32; 1, 2 in FP64), else 1
-// (measured fastest for 8 RHS on 32^3x64 in FP32: 177 ms of operator time per solve against 207 ms
-// for 2 and 265 ms for 4)
+// below kShWarps RHS (measured for 8 RHS on 32^3x64 in FP32 before the shared-link kernel: 177 ms of
+// operator time per solve against 207 ms for 2 and 265 ms for 4)
+// -1 (kRhsShared) selects the shared-link kernel, the default from kShWarps right-hand sides on
+// (fewer leave warps of its blocks idle). Returns 0 for a request this precision does not support.
 int wilson_rhs_block(int prec, int R, int requested) {
   const int cap = prec == QCD_PREC_DOUBLE ? 2 : 4;
-  if (requested > 0) return (requested == 1 || requested == 2 || requested == 4) && requested <= cap ? requested : -1;
-  return 1;
+  if (requested == kRhsShared) return kRhsShared;
+  if (requested > 0) return (requested == 1 || requested == 2 || requested == 4) && requested <= cap ? requested : 0;
+  return R >= kShWarps ? kRhsShared : 1;
 }
 
 template <int PREC, int RB>
@@ -917,11 +1017,38 @@ static int wilson_op_mrhs_typed(const qcd_lattice* lat, void* out, const void* i
   return QCD_OK;
 }
 
+template <int PREC>
+static int wilson_op_mrhs_shared(const qcd_lattice* lat, void* out, const void* in, int R, double kappa, int mode,
+                                 cudaStream_t st) {
+  using FT = WField<PREC>;
+  const Geom g = make_geom(lat);
+  const int V = (int)lat->V;
+  auto U = wl<PREC>(lat->wilson_links[PREC], V);
+  const FT fin = wf<PREC>(const_cast<void*>(in), V), fout = wf<PREC>(out, V);
+  if (mode == 0) {
+    auto k = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, false, WOpM<FT, 0>>;
+    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 0>{fin, fout, kappa, nullptr});
+  } else if (mode == 1) {
+    auto k = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, false, WOpM<FT, 1>>;
+    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 1>{fin, fout, kappa, nullptr});
+  } else {
+    auto k = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, true, WOpM<FT, 2>>;
+    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 2>{fin, fout, kappa, nullptr});
+  }
+  QCD_CUDA(cudaGetLastError());
+  return QCD_OK;
+}
+
 int launch_wilson_op_mrhs(const qcd_lattice* lat, void* out, const void* in, int R, double kappa, int mode, int prec,
                           cudaStream_t st) {
-  // the default register block (1)
-  if (prec == QCD_PREC_DOUBLE) return wilson_op_mrhs_typed<QCD_PREC_DOUBLE, 1>(lat, out, in, R, kappa, mode, st);
-  if (prec == QCD_PREC_SINGLE) return wilson_op_mrhs_typed<QCD_PREC_SINGLE, 1>(lat, out, in, R, kappa, mode, st);
+  // the default kernel for R right-hand sides: shared links from kShWarps on, else register block 1
+  const bool shared = wilson_rhs_block(prec, R, 0) == kRhsShared;
+  if (prec == QCD_PREC_DOUBLE)
+    return shared ? wilson_op_mrhs_shared<QCD_PREC_DOUBLE>(lat, out, in, R, kappa, mode, st)
+                  : wilson_op_mrhs_typed<QCD_PREC_DOUBLE, 1>(lat, out, in, R, kappa, mode, st);
+  if (prec == QCD_PREC_SINGLE)
+    return shared ? wilson_op_mrhs_shared<QCD_PREC_SINGLE>(lat, out, in, R, kappa, mode, st)
+                  : wilson_op_mrhs_typed<QCD_PREC_SINGLE, 1>(lat, out, in, R, kappa, mode, st);
   return QCD_ERR_UNSUPPORTED;
 }
 
@@ -954,9 +1081,16 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
   const FH xh = wf<HI>(w.x_hi, V), t64 = wf<HI>(w.t64, V);
   const int grid = one_wave_grid(V, wilson_kernel<WLinks<HI>, FH, true, WEpiResidual<FH, FT, false>>);
   const int grid_ru = one_wave_grid(V, wilson_kernel<WLinks<PREC>, FT, true, WEpiReliableInner<FT>>);
-  auto K1 = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RB, WEpiT<FT>>;
-  auto K2 = wilson_mrhs_kernel<WLinks<PREC>, FT, true, RB, WEpiUpdate<FT, FT>>;
-  const dim3 gp = w_grid(w_p_kernel<FT>, V, R), g1 = w_grid(K1, V, 1), g2 = w_grid(K2, V, 1);
+  // the two operator launches of an iteration: the shared-link kernel (RB == kRhsShared) or the
+  // register-blocked one
+  constexpr int RBK = RB == kRhsShared ? 1 : RB;
+  auto K1 = wilson_mrhs_kernel<WLinks<PREC>, FT, false, RBK, WEpiT<FT>>;
+  auto K2 = wilson_mrhs_kernel<WLinks<PREC>, FT, true, RBK, WEpiUpdate<FT, FT>>;
+  auto S1 = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, false, WEpiT<FT>>;
+  auto S2 = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, true, WEpiUpdate<FT, FT>>;
+  const dim3 gp = w_grid(w_p_kernel<FT>, V, R);
+  const dim3 g1 = RB == kRhsShared ? dim3(w_shared_grid(S1, V)) : w_grid(K1, V, 1);
+  const dim3 g2 = RB == kRhsShared ? dim3(w_shared_grid(S2, V)) : w_grid(K2, V, 1);
   const size_t cbytes = (size_t)V * 12 * sizeof(double2);  // one canonical spinor field
   long long launches = 0;
 
@@ -1063,8 +1197,13 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
     for (int i = 0; i < k; ++i) {
       w_p_kernel<<<gp, kBlock, 0, st>>>(V, r, p, w.sc);
       if (profile) cudaEventRecord(ev[2 * i], st);
-      K1<<<g1, kBlock, 0, st>>>(g, V, U, p, R, WEpiT<FT>{p, t, kappa, w.sc, w.partials});
-      K2<<<g2, kBlock, 0, st>>>(g, V, U, t, R, WEpiUpdate<FT, FT>{t, p, r, xl, kappa, w.sc, w.partials});
+      if (RB == kRhsShared) {
+        S1<<<g1, kShThreads, 0, st>>>(g, V, U, p, R, WEpiT<FT>{p, t, kappa, w.sc, w.partials});
+        S2<<<g2, kShThreads, 0, st>>>(g, V, U, t, R, WEpiUpdate<FT, FT>{t, p, r, xl, kappa, w.sc, w.partials});
+      } else {
+        K1<<<g1, kBlock, 0, st>>>(g, V, U, p, R, WEpiT<FT>{p, t, kappa, w.sc, w.partials});
+        K2<<<g2, kBlock, 0, st>>>(g, V, U, t, R, WEpiUpdate<FT, FT>{t, p, r, xl, kappa, w.sc, w.partials});
+      }
       if (profile) cudaEventRecord(ev[2 * i + 1], st);
       launches += 3;
       op_launches += 2;
@@ -1118,21 +1257,24 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
 int run_wilson_cgnr(qcd_lattice* lat, int R, void* x, const void* b, double kappa, double tol, int max_iter,
                     const qcd_solver_opts& o, void* ws, qcd_solve_info* info, cudaStream_t st) {
   const int rb = wilson_rhs_block(o.prec_inner, R, o.rhs_block);
-  if (rb < 1) {
+  if (rb == 0) {
     set_error("unsupported RHS block %d for Wilson precision %d", o.rhs_block, o.prec_inner);
     return QCD_ERR_INVALID_ARG;
   }
-  constexpr int D = QCD_PREC_DOUBLE, S = QCD_PREC_SINGLE, DF = QCD_PREC_DF64;
+  constexpr int D = QCD_PREC_DOUBLE, S = QCD_PREC_SINGLE, DF = QCD_PREC_DF64, SH = kRhsShared;
   if (o.prec_inner == D) {
+    if (rb == SH) return wilson_cgnr_typed<D, D, SH>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
     if (rb == 1) return wilson_cgnr_typed<D, D, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
     return wilson_cgnr_typed<D, D, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
   }
   if (o.prec_inner == S && o.prec_outer == D) {
+    if (rb == SH) return wilson_cgnr_typed<S, D, SH>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
     if (rb == 1) return wilson_cgnr_typed<S, D, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
     if (rb == 2) return wilson_cgnr_typed<S, D, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
     return wilson_cgnr_typed<S, D, 4>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
   }
   if (o.prec_inner == S && o.prec_outer == DF) {
+    if (rb == SH) return wilson_cgnr_typed<S, DF, SH>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
     if (rb == 1) return wilson_cgnr_typed<S, DF, 1>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
     if (rb == 2) return wilson_cgnr_typed<S, DF, 2>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);
     return wilson_cgnr_typed<S, DF, 4>(lat, R, x, b, kappa, tol, max_iter, o, ws, info, st);

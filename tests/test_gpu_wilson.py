@@ -212,7 +212,7 @@ def _op_mrhs(rig, psis, kappa, op, prec):
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 6, 8)])
-@pytest.mark.parametrize("nrhs", [1, 2, 3, 5])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 5, 8, 11])
 def test_wilson_op_mrhs_matches_oracle(H, dims, nrhs):
     """Every RHS of the multi-RHS operator (ragged last register block included) against the oracle."""
     U = I.make_links(dims, kind="haar", seed=1)
@@ -251,7 +251,9 @@ def _cgnr_mrhs(rig, bs, kappa, tol=1e-10, prec=Q.QCD_PREC_SINGLE, rhs_block=0, m
     (Q.QCD_PREC_SINGLE, 0, Q.QCD_PREC_DOUBLE), (Q.QCD_PREC_SINGLE, 1, Q.QCD_PREC_DOUBLE),
     (Q.QCD_PREC_SINGLE, 2, Q.QCD_PREC_DOUBLE), (Q.QCD_PREC_SINGLE, 4, Q.QCD_PREC_DOUBLE),
     (Q.QCD_PREC_DOUBLE, 0, Q.QCD_PREC_DOUBLE), (Q.QCD_PREC_DOUBLE, 2, Q.QCD_PREC_DOUBLE),
-    (Q.QCD_PREC_SINGLE, 0, Q.QCD_PREC_DF64), (Q.QCD_PREC_SINGLE, 2, Q.QCD_PREC_DF64)])
+    (Q.QCD_PREC_SINGLE, 0, Q.QCD_PREC_DF64), (Q.QCD_PREC_SINGLE, 2, Q.QCD_PREC_DF64),
+    (Q.QCD_PREC_SINGLE, -1, Q.QCD_PREC_DOUBLE), (Q.QCD_PREC_DOUBLE, -1, Q.QCD_PREC_DOUBLE),
+    (Q.QCD_PREC_SINGLE, -1, Q.QCD_PREC_DF64)])
 def test_wilson_cgnr_mrhs_matches_oracle(H, prec, rhs_block, outer):
     dims, kappa = (4, 4, 4, 4), 0.125
     U = I.make_links(dims, kind="haar", seed=1)
@@ -268,6 +270,22 @@ def test_wilson_cgnr_mrhs_matches_oracle(H, prec, rhs_block, outer):
         assert H.rel(x[k], ref["x"]) <= 1e-7
         if prec == Q.QCD_PREC_SINGLE:
             assert infos[k]["reliable_updates"] >= 1
+
+
+@pytest.mark.parametrize("nrhs", [9, 16])
+def test_wilson_cgnr_shared_link_kernel_many_rhs(H, nrhs):
+    """The shared-link multi-RHS kernel (the default from 8 RHS on) with one and two RHS per warp and
+    a ragged last tile (2x4x6x6 = 288 sites = 9 tiles of 32): every RHS against the oracle."""
+    dims, kappa = (2, 4, 6, 6), 0.125
+    U = I.make_links(dims, kind="haar", seed=1)
+    bs = list(_spinors(dims, nrhs, seed0=30))
+    rig = WRig(H, dims, U)
+    rc, infos, x = _cgnr_mrhs(rig, bs, kappa, 1e-10, Q.QCD_PREC_SINGLE, 0)
+    assert rc == Q.QCD_OK, infos
+    for k in (0, 7, nrhs - 1):
+        assert infos[k]["converged"] and infos[k]["true_rel_residual"] <= 1e-10
+        ref = W.cgnr(U, bs[k], dims, kappa, tol=1e-12, max_iter=10000)
+        assert H.rel(x[k], ref["x"]) <= 1e-7
 
 
 def test_wilson_cgnr_mrhs_each_rhs_stops_on_its_own(H):
