@@ -1034,14 +1034,16 @@ def run_gpu_wilson(args, wl):
     ms_prof, runs_prof = timed(1, max(1, min(args.steps, 3)), profile=True)
     ms_e2e, runs_e2e = timed(1, args.steps, host_io=True)
     ms_oth, runs_oth = None, None
-    if not args.no_variant:
+    if not args.no_variant and not args.no_legs:
         solve(1, hi=other)
         ms_oth, runs_oth = timed(1, max(1, min(args.steps, 2)), hi=other)
-    del ws[1]
-    opts.prec_inner, opts.prec_outer = 0, 0
-    ws[0] = lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))
-    solve(0)
-    ms64, runs64 = timed(0, max(1, min(args.steps, 2)))
+    ms64, runs64 = None, None
+    if not args.no_legs:
+        del ws[1]
+        opts.prec_inner, opts.prec_outer = 0, 0
+        ws[0] = lat.empty_bytes(Q.qcd_wilson_workspace_bytes(lat.handle, opts, R))
+        solve(0)
+        ms64, runs64 = timed(0, max(1, min(args.steps, 2)))
 
     # operator kernels alone (CUDA events on the launching stream, L2 flushed before each)
     with torch.cuda.stream(stream):
@@ -1069,16 +1071,20 @@ def run_gpu_wilson(args, wl):
             t.append(e0.elapsed_time(e1))
         return statistics.median(t)
 
-    t_op64 = op_time(0, 1)
-    t_opdf = op_time(3, 1)
-    t_op32 = op_time(1, 1)
-    t_op32_r = op_time(1, R) if R > 1 else t_op32
+    if args.no_legs:
+        t_op64 = t_opdf = t_op32 = t_op32_r = float("nan")
+    else:
+        t_op64 = op_time(0, 1)
+        t_opdf = op_time(3, 1)
+        t_op32 = op_time(1, 1)
+        t_op32_r = op_time(1, R) if R > 1 else t_op32
 
     (total_ms, total_ms_e2e), (fl0, fl1) = reduce_over_ranks([sum(ms), sum(ms_e2e)],
                                                               [flops_of(runs), flops_of(runs_e2e)])
     value = fl0 / (total_ms * 1e-3) / 1e9
     e2e_value = fl1 / (total_ms_e2e * 1e-3) / 1e9
-    t_mixed, t_64 = sum(ms) / len(ms), sum(ms64) / len(ms64)
+    t_mixed = sum(ms) / len(ms)
+    t_64 = sum(ms64) / len(ms64) if ms64 else float("nan")
 
     # roofline of the FP32 operator launches inside the solve (K1: t = M p, K2: M^dagger t + update).
     # Algorithmic bytes: the links once per launch (4 links x 72 B per site, FP32 recon-18) and, per
@@ -1113,9 +1119,9 @@ def run_gpu_wilson(args, wl):
         "cg": {"iterations": [i["iterations"] for i in runs[-1]],
                "reliable_updates": [i["reliable_updates"] for i in runs[-1]],
                "max_true_rel_residual": max(i["true_rel_residual"] for i in runs[-1]),
-               "time_to_solution_ms": round(t_mixed, 4), "plain_fp64_cgnr_ms": round(t_64, 4),
-               "plain_fp64_iterations": [i["iterations"] for i in runs64[-1]],
-               "speedup_vs_plain_fp64_cgnr": round(t_64 / t_mixed, 3)},
+               "time_to_solution_ms": round(t_mixed, 4), "plain_fp64_cgnr_ms": round(t_64, 4) if ms64 else None,
+               "plain_fp64_iterations": [i["iterations"] for i in runs64[-1]] if runs64 else None,
+               "speedup_vs_plain_fp64_cgnr": round(t_64 / t_mixed, 3) if ms64 else None},
         "roofline": {"bound": "hbm", "kernel": "wilson_mrhs_kernel (CGNR K1+K2 launches, FP32)",
                      "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
