@@ -447,9 +447,36 @@ struct WShMinBlocks {  // 256-thread blocks per SM: 2 (128 registers) for FP32, 
   static constexpr int value = sizeof(T) == 4 ? 2 : 1;
 };
 
+// The order in which the tiles visit the sites: rows of L0 sites taken in (x1, x2 within a chunk of
+// zc, x3, chunk) order instead of lexicographically. A site's x3 (t) neighbours then come
+// L0 L1 zc sites later in the sweep instead of a whole L0 L1 L2 time slice later, and are still in
+// L2 when they are needed; only the x2 hops that cross a chunk boundary (1/zc of them) reach back
+// further. Memory layout and coalescing are unchanged (a tile is 32 consecutive sites of a row
+// when L0 >= 32). Returns the site and its coordinates for sweep index j.
+__device__ __forceinline__ int w_sweep_site(const Geom& g, int zc, int j, int c[4]) {
+  c[0] = j % g.L0;
+  int r = j / g.L0;
+  c[1] = r % g.L1; r /= g.L1;
+  const int zz = r % zc; r /= zc;
+  c[3] = r % g.L3;
+  c[2] = (r / g.L3) * zc + zz;
+  return c[0] + g.L0 * (c[1] + g.L1 * (c[2] + g.L2 * c[3]));
+}
+
+// The x2 chunk of the sweep: the largest of 16, 8, 4, 2 dividing L2 whose L0 L1 zc sites stay
+// within 4096, else 1 (lexicographic). Measured on GB300, 32^3x64 x 8 RHS (FP32 CGNR, df64 reliable
+// updates), per solve: lexicographic 374 ms, zc = 16 (16384 sites) 366 ms, 8: 357 ms, 4: 354 ms; a
+// site's input is used over twice the chunk distance in the sweep, and ~8 MB of fields and links
+// per 4096 sites have to stay in L2 meanwhile.
+inline int w_sweep_chunk(const Geom& g) {
+  for (int zc : {16, 8, 4, 2})
+    if (g.L2 % zc == 0 && (long long)g.L0 * g.L1 * zc <= 4096) return zc;
+  return 1;
+}
+
 template <class LinksT, class FieldT, bool G5IN, class Epi>
 __global__ void __launch_bounds__(kShThreads, WShMinBlocks<typename LinksT::T>::value)
-    wilson_mrhs_shared_kernel(Geom g, int V, LinksT U, FieldT in, int nrhs, Epi epi) {
+    wilson_mrhs_shared_kernel(Geom g, int V, LinksT U, FieldT in, int nrhs, Epi epi, int zc) {
   using T = typename LinksT::T;
   using A = typename Accum<T>::type;
   __shared__ __align__(16) unsigned char sl_raw[kShWarps * 9 * kShTile * sizeof(cplx<T>)];
@@ -462,11 +489,11 @@ __global__ void __launch_bounds__(kShThreads, WShMinBlocks<typename LinksT::T>::
   A part[2] = {A(0), A(0)};
   const int ntiles = (V + kShTile - 1) / kShTile;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int i = tile * kShTile + lane;
-    const bool valid = i < V;
+    const int j = tile * kShTile + lane;
+    const bool valid = j < V;
     int c[4] = {0, 0, 0, 0};
+    const int i = valid ? w_sweep_site(g, zc, j, c) : 0;
     if (valid) {
-      full_site(g, i, c);
       const int mu = w >> 1, dir = w & 1;
       const su3<T> L = U.load(mu, dir == 0 ? i : w_neighbour(g, i, c, mu, 1));
 #pragma unroll
@@ -1027,13 +1054,16 @@ static int wilson_op_mrhs_shared(const qcd_lattice* lat, void* out, const void* 
   const FT fin = wf<PREC>(const_cast<void*>(in), V), fout = wf<PREC>(out, V);
   if (mode == 0) {
     auto k = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, false, WOpM<FT, 0>>;
-    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 0>{fin, fout, kappa, nullptr});
+    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 0>{fin, fout, kappa, nullptr},
+                                                   w_sweep_chunk(g));
   } else if (mode == 1) {
     auto k = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, false, WOpM<FT, 1>>;
-    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 1>{fin, fout, kappa, nullptr});
+    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 1>{fin, fout, kappa, nullptr},
+                                                   w_sweep_chunk(g));
   } else {
     auto k = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, true, WOpM<FT, 2>>;
-    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 2>{fin, fout, kappa, nullptr});
+    k<<<w_shared_grid(k, V), kShThreads, 0, st>>>(g, V, U, fin, R, WOpM<FT, 2>{fin, fout, kappa, nullptr},
+                                                   w_sweep_chunk(g));
   }
   QCD_CUDA(cudaGetLastError());
   return QCD_OK;
@@ -1089,6 +1119,7 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
   auto S1 = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, false, WEpiT<FT>>;
   auto S2 = wilson_mrhs_shared_kernel<WLinks<PREC>, FT, true, WEpiUpdate<FT, FT>>;
   const dim3 gp = w_grid(w_p_kernel<FT>, V, R);
+  const int zc = w_sweep_chunk(g);
   const dim3 g1 = RB == kRhsShared ? dim3(w_shared_grid(S1, V)) : w_grid(K1, V, 1);
   const dim3 g2 = RB == kRhsShared ? dim3(w_shared_grid(S2, V)) : w_grid(K2, V, 1);
   const size_t cbytes = (size_t)V * 12 * sizeof(double2);  // one canonical spinor field
@@ -1198,8 +1229,8 @@ static int wilson_cgnr_typed(qcd_lattice* lat, int R, void* x, const void* b, do
       w_p_kernel<<<gp, kBlock, 0, st>>>(V, r, p, w.sc);
       if (profile) cudaEventRecord(ev[2 * i], st);
       if (RB == kRhsShared) {
-        S1<<<g1, kShThreads, 0, st>>>(g, V, U, p, R, WEpiT<FT>{p, t, kappa, w.sc, w.partials});
-        S2<<<g2, kShThreads, 0, st>>>(g, V, U, t, R, WEpiUpdate<FT, FT>{t, p, r, xl, kappa, w.sc, w.partials});
+        S1<<<g1, kShThreads, 0, st>>>(g, V, U, p, R, WEpiT<FT>{p, t, kappa, w.sc, w.partials}, zc);
+        S2<<<g2, kShThreads, 0, st>>>(g, V, U, t, R, WEpiUpdate<FT, FT>{t, p, r, xl, kappa, w.sc, w.partials}, zc);
       } else {
         K1<<<g1, kBlock, 0, st>>>(g, V, U, p, R, WEpiT<FT>{p, t, kappa, w.sc, w.partials});
         K2<<<g2, kBlock, 0, st>>>(g, V, U, t, R, WEpiUpdate<FT, FT>{t, p, r, xl, kappa, w.sc, w.partials});
