@@ -28,10 +28,12 @@ __global__ void __launch_bounds__(kBlock) force_kernel(Geom g, const double2* __
     int c[4];
     {
       int r = lex;
-      c[0] = r % g.L0; r /= g.L0;
-      c[1] = r % g.L1; r /= g.L1;
-      c[2] = r % g.L2;
-      c[3] = r / g.L2;
+      const int r0 = fdiv(r, g.d0);
+      c[0] = r - r0 * g.L0;
+      const int r1 = fdiv(r0, g.d1);
+      c[1] = r0 - r1 * g.L1;
+      c[3] = fdiv(r1, g.d2);
+      c[2] = r1 - c[3] * g.L2;
     }
     const int L[4] = {g.L0, g.L1, g.L2, g.L3};
     const int st[4] = {1, g.L0, g.L0 * g.L1, g.L0 * g.L1 * g.L2};

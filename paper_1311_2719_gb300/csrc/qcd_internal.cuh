@@ -49,10 +49,43 @@ namespace qcd {
 // ------------------------------------------------------------------------------------------
 // Device geometry: even-odd index <-> coordinates and neighbours (the paper's iup/idn, computed).
 // ------------------------------------------------------------------------------------------
+// Division of a non-negative int by a run-time constant d >= 1 as a multiply-high and shifts
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994, §4:
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0)
+// with t = the high half of m n; exact for every 32-bit unsigned n). Every site kernel turns its
+// index into coordinates with three divisions and two remainders by the extents; compiled as
+// integer divisions they are long instruction sequences in kernels that are issue-limited.
+struct FastDiv {
+  unsigned d, m;
+  int s1, s2;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (unsigned)((((1ull << l) - d) << 32) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+__host__ __device__ __forceinline__ unsigned umulhi32(unsigned a, unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (unsigned)(((unsigned long long)a * b) >> 32);
+#endif
+}
+__host__ __device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+  const unsigned t = umulhi32(f.m, (unsigned)n);
+  return (int)((t + (((unsigned)n - t) >> f.s1)) >> f.s2);
+}
+
 struct Geom {
   int L0, L1, L2, L3;
   int Vh;
   float tbc;  // +1 or -1
+  FastDiv d0, d1, d2, d3;  // division by L0 .. L3
 };
 
 inline Geom make_geom(const qcd_lattice* lat) {
@@ -60,6 +93,10 @@ inline Geom make_geom(const qcd_lattice* lat) {
   g.L0 = lat->L[0]; g.L1 = lat->L[1]; g.L2 = lat->L[2]; g.L3 = lat->L[3];
   g.Vh = (int)lat->Vh;
   g.tbc = (float)lat->tbc;
+  g.d0 = make_fastdiv((unsigned)g.L0);
+  g.d1 = make_fastdiv((unsigned)g.L1);
+  g.d2 = make_fastdiv((unsigned)g.L2);
+  g.d3 = make_fastdiv((unsigned)g.L3);
   return g;
 }
 
@@ -73,11 +110,12 @@ struct Site {
 __device__ __forceinline__ Site site_of(const Geom& g, int k, int par) {
   Site s;
   int j = 2 * k;
-  int t = j / g.L0;
+  int t = fdiv(j, g.d0);
   int x0e = j - t * g.L0;
-  s.x1 = t % g.L1; t /= g.L1;
-  s.x2 = t % g.L2;
-  s.x3 = t / g.L2;
+  const int t1 = fdiv(t, g.d1);
+  s.x1 = t - t1 * g.L1;
+  s.x3 = fdiv(t1, g.d2);
+  s.x2 = t1 - s.x3 * g.L2;
   s.x0 = x0e + ((s.x1 + s.x2 + s.x3 + par) & 1);
   s.lex = j + (s.x0 - x0e);
   return s;

@@ -213,10 +213,12 @@ size_t wlinks_bytes(int prec, long long V) {
 // ---------------------------------------------------------------- geometry (full lattice)
 __device__ __forceinline__ void full_site(const Geom& g, int i, int c[4]) {
   int t = i;
-  c[0] = t % g.L0; t /= g.L0;
-  c[1] = t % g.L1; t /= g.L1;
-  c[2] = t % g.L2;
-  c[3] = t / g.L2;
+  const int t0 = fdiv(t, g.d0);
+  c[0] = t - t0 * g.L0;
+  const int t1 = fdiv(t0, g.d1);
+  c[1] = t0 - t1 * g.L1;
+  c[3] = fdiv(t1, g.d2);
+  c[2] = t1 - c[3] * g.L2;
 }
 
 // ---------------------------------------------------------------- the hopping term at site i
@@ -454,16 +456,19 @@ struct WShMinBlocks {  // 256-thread blocks per SM: 2 (128 registers) for FP32, 
 // further. Memory layout and coalescing are unchanged (a tile is 32 consecutive sites of a row
 // when L0 >= 32). Returns the site and its coordinates for sweep index j.
 __device__ __forceinline__ int w_sweep_site(const Geom& g, int zc, int j, int c[4]) {
-  c[0] = j % g.L0;
-  int r = j / g.L0;
-  c[1] = r % g.L1; r /= g.L1;
-  const int zz = r % zc; r /= zc;
-  c[3] = r % g.L3;
-  c[2] = (r / g.L3) * zc + zz;
+  int r = fdiv(j, g.d0);
+  c[0] = j - r * g.L0;
+  const int r1 = fdiv(r, g.d1);
+  c[1] = r - r1 * g.L1;
+  const int zz = r1 & (zc - 1);  // zc is a power of two
+  r = r1 >> (__ffs(zc) - 1);
+  const int r3 = fdiv(r, g.d3);
+  c[3] = r - r3 * g.L3;
+  c[2] = r3 * zc + zz;
   return c[0] + g.L0 * (c[1] + g.L1 * (c[2] + g.L2 * c[3]));
 }
 
-// The x2 chunk of the sweep: the largest of 16, 8, 4, 2 dividing L2 whose L0 L1 zc sites stay
+// The x2 chunk of the sweep (a power of two): the largest of 16, 8, 4, 2 dividing L2 whose L0 L1 zc sites stay
 // within 4096, else 1 (lexicographic). Measured on GB300, 32^3x64 x 8 RHS (FP32 CGNR, df64 reliable
 // updates), per solve: lexicographic 374 ms, zc = 16 (16384 sites) 366 ms, 8: 357 ms, 4: 354 ms; a
 // site's input is used over twice the chunk distance in the sweep, and ~8 MB of fields and links
