@@ -237,6 +237,84 @@ __device__ __forceinline__ cvec3<T> adj_mul(const su3<T>& U, const cvec3<T>& x) 
   return w;
 }
 
+// ---- df64 colour products with lazy accumulation. An output component of U x is a sum of six
+// real products plus the accumulator. Each product a*b is formed exactly as p + e (e by FMA, the
+// cross terms a.hi b.lo + a.lo b.hi folded into e); the six p's and the accumulator's hi part are
+// added by two-sums in a fixed tree, every rounding error and e and the accumulator's lo part are
+// collected in one float, and the result is renormalised once. The generic form renormalises after
+// every multiply-add, a chain of six dependent 14-operation steps per component; here the products
+// are independent and the chain is three two-sums deep. Error: a few units of 2^-48 of the largest
+// term, as before.
+__device__ __forceinline__ void df64_prod(df64 a, df64 b, float& p, float& e) {
+  p = __fmul_rn(a.hi, b.hi);
+  e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+}
+// c + sum_k a_k b_k over six terms
+__device__ __forceinline__ df64 df64_dot6_add(const df64 (&a)[6], const df64 (&b)[6], df64 c) {
+  float p[6], e[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) df64_prod(a[k], b[k], p[k], e[k]);
+  float s01, t01, s23, t23, s45, t45, s03, t03, s05, t05, s, t;
+  two_sum(p[0], p[1], s01, t01);
+  two_sum(p[2], p[3], s23, t23);
+  two_sum(p[4], p[5], s45, t45);
+  two_sum(s01, s23, s03, t03);
+  two_sum(s03, s45, s05, t05);
+  two_sum(c.hi, s05, s, t);
+  const float err = __fadd_rn(
+      __fadd_rn(__fadd_rn(__fadd_rn(e[0], e[1]), __fadd_rn(e[2], e[3])), __fadd_rn(__fadd_rn(e[4], e[5]), c.lo)),
+      __fadd_rn(__fadd_rn(__fadd_rn(t01, t23), __fadd_rn(t45, t03)), __fadd_rn(t05, t)));
+  df64 r;
+  quick_two_sum(s, err, r.hi, r.lo);
+  return r;
+}
+
+// acc += U x
+__device__ __forceinline__ void mul_add(cvec3<df64>& acc, const su3<df64>& U, const cvec3<df64>& x) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const df64 ure[6] = {U.e[a][0].re, -U.e[a][0].im, U.e[a][1].re, -U.e[a][1].im, U.e[a][2].re, -U.e[a][2].im};
+    const df64 xre[6] = {x.c[0].re, x.c[0].im, x.c[1].re, x.c[1].im, x.c[2].re, x.c[2].im};
+    const df64 uim[6] = {U.e[a][0].re, U.e[a][0].im, U.e[a][1].re, U.e[a][1].im, U.e[a][2].re, U.e[a][2].im};
+    const df64 xim[6] = {x.c[0].im, x.c[0].re, x.c[1].im, x.c[1].re, x.c[2].im, x.c[2].re};
+    acc.c[a].re = df64_dot6_add(ure, xre, acc.c[a].re);
+    acc.c[a].im = df64_dot6_add(uim, xim, acc.c[a].im);
+  }
+}
+
+// acc -= U^dagger x: conj(U_ba) x_b = (U_re x_re + U_im x_im) + i (U_re x_im - U_im x_re)
+__device__ __forceinline__ void adj_mul_sub(cvec3<df64>& acc, const su3<df64>& U, const cvec3<df64>& x) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const df64 ure[6] = {-U.e[0][a].re, -U.e[0][a].im, -U.e[1][a].re, -U.e[1][a].im, -U.e[2][a].re, -U.e[2][a].im};
+    const df64 xre[6] = {x.c[0].re, x.c[0].im, x.c[1].re, x.c[1].im, x.c[2].re, x.c[2].im};
+    const df64 uim[6] = {-U.e[0][a].re, U.e[0][a].im, -U.e[1][a].re, U.e[1][a].im, -U.e[2][a].re, U.e[2][a].im};
+    const df64 xim[6] = {x.c[0].im, x.c[0].re, x.c[1].im, x.c[1].re, x.c[2].im, x.c[2].re};
+    acc.c[a].re = df64_dot6_add(ure, xre, acc.c[a].re);
+    acc.c[a].im = df64_dot6_add(uim, xim, acc.c[a].im);
+  }
+}
+
+// w = U x
+__device__ __forceinline__ cvec3<df64> mul(const su3<df64>& U, const cvec3<df64>& x) {
+  cvec3<df64> w;
+  zero(w);
+  mul_add(w, U, x);
+  return w;
+}
+
+// w = U^dagger x
+__device__ __forceinline__ cvec3<df64> adj_mul(const su3<df64>& U, const cvec3<df64>& x) {
+  cvec3<df64> w;
+  zero(w);
+  adj_mul_sub(w, U, x);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) w.c[a] = {-w.c[a].re, -w.c[a].im};
+  return w;
+}
+
 // acc += s * w
 template <typename T>
 __device__ __forceinline__ void axpy(cvec3<T>& acc, T s, const cvec3<T>& w) {
