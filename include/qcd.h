@@ -165,7 +165,10 @@ QCD_API void qcd_solver_opts_default(qcd_solver_opts* opts);
  * (device, qcd_links_bytes(lat, prec, recon) bytes) and register it as the links used by every
  * later call at precision `prec`. Recon 18 folds 1/2 * eta * zeta into the stored links; recon 12
  * stores the first two rows and the kernels rebuild the third as conj(row0 x row1) and apply
- * the phases from the site coordinates. The caller keeps `packed_dev` alive. */
+ * the phases from the site coordinates. QCD_PREC_HALF links are 16-bit fixed point (every real v
+ * of the two rows as round(v * 2^15) + 2^15, saturated to [0, 65535]; absolute error <= 2^-16,
+ * 2^-15 for v within 2^-16 of 1).
+ * The caller keeps `packed_dev` alive. */
 QCD_API int qcd_load_links(qcd_lattice* lat, const void* links_dev, void* packed_dev, int prec, int recon,
                    void* stream);
 

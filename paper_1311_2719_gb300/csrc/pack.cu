@@ -49,7 +49,7 @@ __global__ void pack_links_kernel(Geom g, const double2* __restrict__ canon, voi
         uint2* ob = (uint2*)((uint4*)out + 8 * (size_t)g.Vh) + (size_t)pm * g.Vh + k;
         unsigned w[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) w[i] = float2_to_u32((float)e[i].x, (float)e[i].y);
+        for (int i = 0; i < 6; ++i) w[i] = float2_to_fx16x2((float)e[i].x, (float)e[i].y);
         *oa = make_uint4(w[0], w[1], w[2], w[3]);
         *ob = make_uint2(w[4], w[5]);
       }
