@@ -45,10 +45,11 @@ WORKLOADS = {
     # the headline: 32^4 Haar, m = 0.01, mixed FP32 recon-12 CG with FP64 reliable updates, with the
     # plain FP64, FP16 and df64 solves, the operators alone and the batched solves on the same line
     "cg32_mixed": dict(kind_solve="mixed32", dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10,
-                       inner="single12",
-                       desc="staggered 32^4 Haar SU(3), m=0.01, mixed CG: FP32 recon-12 inner, FP64 reliable updates "
-                            "every 100 iterations, to true rel. residual 1e-10 (vs plain FP64, FP16 recon-12 and "
-                            "df64 on the same lattice; 24^4 x 16 RHS and 64-lattice batches beside)"),
+                       inner="half12",
+                       desc="staggered 32^4 Haar SU(3), m=0.01, mixed CG: 16-bit recon-12 inner (fixed-point links, "
+                            "FP16 vectors with a per-site scale, FP32 arithmetic), FP64 reliable updates every 100 "
+                            "iterations, to true rel. residual 1e-10 (vs plain FP64, FP32 recon-12 and df64 on the "
+                            "same lattice; 24^4 x 16 RHS and 64-lattice batches beside)"),
     # the 16^4 FP64 workload: Haar links, m = 0.1, plain FP64 even-odd CG
     "cg16_fp64": dict(dims=(16, 16, 16, 16), kind="haar", mass=0.1, tol=1e-10, inner="double",
                       desc="staggered 16^4 Haar SU(3), m=0.1, plain FP64 even-odd CG to true rel. residual 1e-10"),
@@ -59,7 +60,8 @@ WORKLOADS = {
     "cg32_single12": dict(dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="single12",
                           desc="staggered 32^4 Haar, m=0.01, mixed CG: FP32 recon-12 inner, FP64 reliable updates"),
     "cg32_half12": dict(dims=(32, 32, 32, 32), kind="haar", mass=0.01, tol=1e-10, inner="half12",
-                        desc="staggered 32^4 Haar, m=0.01, mixed CG: FP16+scale recon-12 inner, FP64 reliable updates"),
+                        desc="staggered 32^4 Haar, m=0.01, mixed CG: 16-bit recon-12 inner (fixed-point links, FP16 "
+                             "vectors), FP64 reliable updates"),
     "cg16_df64": dict(dims=(16, 16, 16, 16), kind="haar", mass=0.1, tol=1e-10, inner="df64",
                       desc="staggered 16^4 Haar SU(3), m=0.1, even-odd CG in df64 (float-float on the FP32 pipes) "
                            "with FP64 reliable updates, to true rel. residual 1e-10"),
@@ -69,6 +71,10 @@ WORKLOADS = {
                             inner="single12", nrhs=16,
                             desc="staggered 24^4 Haar, m=0.05, 16 RHS in one multi-RHS CG: FP32 recon-12 inner, "
                                  "FP64 reliable updates"),
+    "mrhs24_half12": dict(kind_solve="mrhs", dims=(24, 24, 24, 24), kind="haar", mass=0.05, tol=1e-10,
+                          inner="half12", nrhs=16,
+                          desc="staggered 24^4 Haar, m=0.05, 16 RHS in one multi-RHS CG: 16-bit recon-12 inner "
+                               "(fixed-point links, FP16 vectors), FP64 reliable updates"),
     "wilson32c64_8rhs": dict(kind_solve="wilson", dims=(32, 32, 32, 64), kind="haar", kappa=0.125, tol=1e-10,
                              inner="single18", nrhs=8,
                              desc="Wilson 32^3x64 Haar SU(3), kappa=0.125, 8 RHS in one multi-RHS CGNR on M^dagger M: "
@@ -98,14 +104,20 @@ WORKLOADS = {
     "force32_fp64": dict(kind_solve="force", dims=(32, 32, 32, 32), mass=0.1, tol=1e-10,
                          desc="staggered fermion force on every link of a 32^4 Haar lattice from the CG's x and "
                               "y = D_oe x (m = 0.1), FP64"),
+    "batch64_half12": dict(kind_solve="batched", n=64, tol=1e-10, inner="half12",
+                           desc="64 independent staggered lattices {4^4,6^4,8^4,8^3x16}, m in [0.02,0.5], one "
+                                "persistent clustered CG launch: 16-bit recon-12 inner (fixed-point links, FP16 "
+                                "vectors), FP64 reliable updates"),
     "batch64_single12": dict(kind_solve="batched", n=64, tol=1e-10, inner="single12",
                              desc="64 independent staggered lattices {4^4,6^4,8^4,8^3x16}, m in [0.02,0.5], one "
                                   "persistent clustered CG launch: FP32 recon-12 inner, FP64 reliable updates"),
 }
 DEFAULT_WORKLOAD = "cg32_mixed"
 PRECS = {"double": (0, 18), "single18": (1, 18), "single12": (1, 12), "half12": (2, 12), "df64": (3, 18)}
+NAMES = {"double": "FP64", "single18": "FP32 recon-18", "single12": "FP32 recon-12",
+         "half12": "16-bit recon-12 (fixed-point links, FP16 vectors)", "df64": "df64"}
 DTYPE = {"double": "f64", "single18": "f32 (FP64 reliable updates)", "single12": "f32 (FP64 reliable updates)",
-         "half12": "f16-storage/f32 (FP64 reliable updates)",
+         "half12": "f32 (16-bit storage: fixed-point links, FP16 vectors; FP64 reliable updates)",
          "df64": "df64 (float-float, 48-bit significand; FP64 reliable updates)"}
 
 
@@ -457,16 +469,17 @@ def sampled_oracle_residual(U, x, b, dims, mass, n_sites=2000, seed=0):
 
 
 def run_gpu_mixed32(args, wl):
-    """32^4 Haar, m = 0.01: the mixed-precision even-odd CG (FP32 recon-12 recursion, FP64 reliable
-    updates) as the headline, with on the same line and the same lattice and source:
+    """32^4 Haar, m = 0.01: the mixed-precision even-odd CG (the workload's inner recursion: 16-bit
+    recon-12 by default, FP64 reliable updates) as the headline, with on the same line and the same
+    lattice and source:
       fp64      - the plain FP64 CG and the mixed solve's speedup over it;
-      half12 / df64 - the FP16+scale recon-12 and the df64 recursions;
+      single12 / half12 / df64 - the other recursions (FP32 recon-12, 16-bit recon-12, df64);
       accuracy  - each solution's FP64 residual recomputed by the oracle at sampled sites, and its
                   distance to the plain FP64 GPU solution;
       operators - each precision's half-lattice operator alone (qcd_dslash, back-to-back launches);
       batched   - the 24^4 x 16 RHS and the 64-lattice solves and their speedups over one-by-one
                   plain FP64 CG.
-    One timed step = qcd_load_links (FP64 and FP32 recon-12) + qcd_cg_solve (CG, y, true residual)."""
+    One timed step = qcd_load_links (FP64 and the inner links) + qcd_cg_solve (CG, y, true residual)."""
     import torch
 
     from paper_1311_2719_gb300 import inputs as I
@@ -543,8 +556,9 @@ def run_gpu_mixed32(args, wl):
     def flops_of(infos):
         return sum(FLOP_PER_SITE * Vh * _half_dslash_count(i) for i in infos)
 
-    # ---- headline: the mixed FP32 recon-12 solve
-    head = "single12"
+    # ---- headline: the workload's mixed solve
+    head = wl["inner"]
+    folded = head == "single12"  # the FP32 recursion forms p = r + beta p inside K1
     for _ in range(args.warmup):
         step(head)
     torch.cuda.synchronize()
@@ -568,7 +582,7 @@ def run_gpu_mixed32(args, wl):
 
     # ---- the other recursions on the same lattice and source
     legs, sols = {}, {head: x_mixed}
-    for inner in (() if args.no_legs else ("double", "half12", "df64")):
+    for inner in (() if args.no_legs else tuple(n for n in ("double", "single12", "half12", "df64") if n != head)):
         if inner == "df64" and args.no_variant:
             continue
         step(inner)
@@ -632,31 +646,37 @@ def run_gpu_mixed32(args, wl):
         del fin, fouts
     del lat2, bufs2
 
-    # ---- roofline of the dominant kernel family: every half-lattice operator launch of the timed
-    # step (the FP32 recon-12 K1/K2 of the recursion and the FP64 ones of the reliable updates, y
-    # and the true residual), charged with ALL of the step's time: a lower bound on their rate that
-    # agrees by construction with the step time.
+    # ---- roofline of the dominant kernel family: every kernel of the timed step's CG iterations (K1,
+    # K2 and, unless K1 forms p itself, the p update) and the FP64 operator launches of the reliable
+    # updates, y and the true residual, charged with ALL of the step's time: a lower bound on their
+    # rate that agrees by construction with the step time.
     i = infos[-1]
     n32 = 2 * i["iterations"]
     n_all = _half_dslash_count(i)
     n64 = n_all - n32
-    k1_32, k2_32 = _k1_k2_bytes(head, folded=True)
+    k1_in, k2_in = _k1_k2_bytes(head, folded=folded)
+    k3_in = 0 if folded else 3 * OP_BYTES[head][1]  # p = r + beta p: r, p read, p written
     k1_64, k2_64 = _k1_k2_bytes("double")
-    alg_step = Vh * (i["iterations"] * (k1_32 + k2_32) + n64 / 2 * (k1_64 + k2_64))
+    alg_step = Vh * (i["iterations"] * (k1_in + k2_in + k3_in) + n64 / 2 * (k1_64 + k2_64))
     per_launch_us = t_mixed * 1e3 / n_all
     achieved = alg_step / (t_mixed * 1e-3) / 1e9
     d_ms, d_n = infos_prof[-1]["dslash_ms"], infos_prof[-1]["dslash_launches"]
     roofline = {
-        "bound": "hbm", "kernel": "dslash_kernel (CG K1+K2 launches, FP32 recon-12; FP64 in the reliable updates)",
+        "bound": "hbm",
+        "kernel": f"dslash_kernel (CG K1+K2 launches, {NAMES[head]}; FP64 in the reliable updates)"
+                  + ("" if folded else " + cg_p_kernel"),
         "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
         "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
         "traffic": ncu_traffic(args.workload),
-        "method": "all of the timed step's time charged to its operator launches (a lower bound on the "
-                  "kernels' rate); per-launch bytes = the mean of K1 and K2 at the launch's precision (the FP32 "
-                  "K1 also forms p = r + beta p: links + r + p_old + p + ap)",
-        "alg_bytes_per_site_k1_k2": [k1_32, k2_32], "alg_bytes_per_site_k1_k2_fp64": [k1_64, k2_64],
-        "alg_bytes_per_step": round(alg_step), "alg_bytes_per_launch_fp32": (k1_32 + k2_32) / 2 * Vh,
-        "check": {"operator_launches": n_all, "fp32_launches": n32, "fp64_launches": n64,
+        "method": "all of the timed step's time charged to its CG kernels (a lower bound on their rate); bytes = "
+                  "links and every vector read or written once per launch at the launch's precision"
+                  + (" (the FP32 K1 also forms p = r + beta p: links + r + p_old + p + ap)" if folded else
+                     " (K1 = links + p + ap, K2 = links + ap + p + r in/out + x in/out, p update = r + p in + p out)")
+                  + "; traffic = ncu DRAM bytes per K1/K2 launch",
+        "alg_bytes_per_site_k1_k2": [k1_in, k2_in], "alg_bytes_per_site_p_update": k3_in,
+        "alg_bytes_per_site_k1_k2_fp64": [k1_64, k2_64],
+        "alg_bytes_per_step": round(alg_step), "alg_bytes_per_launch_inner": (k1_in + k2_in) / 2 * Vh,
+        "check": {"operator_launches": n_all, "inner_launches": n32, "fp64_launches": n64,
                   "per_launch_us": round(per_launch_us, 3),
                   "launches_x_per_launch_ms": round(n_all * per_launch_us / 1e3, 4),
                   "ms_per_step": round(t_mixed, 4),
@@ -668,7 +688,7 @@ def run_gpu_mixed32(args, wl):
     # ---- config 4: the multi-RHS and many-lattice solves (their own lattices and sources)
     batched = {}
     if not args.no_batched and not args.no_legs:
-        for key in ("mrhs24_single12", "batch64_single12"):
+        for key in ("mrhs24_half12", "batch64_half12"):
             # launch shapes chosen by the library's autotuner first (outside the timed steps)
             bl = batched_leg(WORKLOADS[key], leg_steps if key.startswith("mrhs") else max(leg_steps, 5), 1, True,
                              key, world, local, fp64_steps=max(1, min(leg_steps, 2)), sample_clocks=False)
@@ -683,13 +703,14 @@ def run_gpu_mixed32(args, wl):
         "config": {"workload": wl["desc"], "dims": list(dims), "mass": mass, "tol": tol, "inner": head,
                    "reliable_update_interval": 100, "parallelism": f"replicas x{world} (no sharding)",
                    "l2": "flushed before every step (512 MB write, outside the timed events)",
-                   "step": "qcd_load_links (FP64 + FP32 recon-12) + qcd_cg_solve (CG, y = D_oe x, FP64 true residual)",
-                   "legs": f"fp64/half12/df64 solves, e2e and batched: {leg_steps} timed steps each after one untimed"},
+                   "step": f"qcd_load_links (FP64 + {NAMES[head]}) + qcd_cg_solve (CG, y = D_oe x, FP64 true residual)",
+                   "legs": f"the other solves, e2e and batched: {leg_steps} timed steps each after one untimed"},
         "cg": {"iterations": i["iterations"], "true_rel_residual": i["true_rel_residual"],
                "reliable_updates": i["reliable_updates"], "time_to_solution_ms": round(t_mixed, 4),
                "half_dslash_per_solve": n_all, "plain_fp64_ms": t_fp64,
                "speedup_vs_fp64": round(t_fp64 / t_mixed, 3) if t_fp64 else None,
-               "speedup_vs_fp64_half12": round(t_fp64 / legs["half12"]["ms_per_step"], 3) if t_fp64 else None},
+               "speedup_vs_fp64_legs": {n: round(t_fp64 / l["ms_per_step"], 3) for n, l in legs.items()
+                                        if n != "double"} if t_fp64 else None},
         "legs": legs,
         "accuracy": accuracy,
         "roofline": roofline,

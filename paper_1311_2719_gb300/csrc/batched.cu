@@ -56,10 +56,11 @@ enum { kBatchOk = 0, kBatchMaxIter = 1, kBatchBreakdown = 2 };
 // total is returned in thread 0 of each CTA only (each CTA's thread 0 adds the same C block
 // sums in rank order, so all of them hold the same bits). `slots` is double-buffered: a slot is
 // rewritten two reductions later, after every CTA has passed the barrier of the one between.
-__device__ __forceinline__ double cluster_total(double part, double* slots, int& buf,
-                                                const cg::cluster_group& cluster) {
-  double v[1] = {part};
-  block_sum<1>(v);
+template <class A>
+__device__ __forceinline__ double cluster_total(A part, double* slots, int& buf, const cg::cluster_group& cluster) {
+  const A x[1] = {part};
+  double v[1];
+  block_sum<1>(x, v);
   if (threadIdx.x == 0) slots[buf] = v[0];
   // make this phase's global writes visible to the cluster before its barrier
   asm volatile("fence.acq_rel.cluster;" ::: "memory");
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
           p.store(k, pv);
           accum(part, norm2(pv));
         }
-        const double pp = cluster_total((double)part, slots, buf, cluster);
+        const double pp = cluster_total(part, slots, buf, cluster);
         // K1: ap = D_oe p
         part = 0;
         for (int k = tid; k < Vh; k += nthreads) {
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
           ap.store(k, acc);
           accum(part, norm2(acc));
         }
-        const double apap = cluster_total((double)part, slots, buf, cluster);
+        const double apap = cluster_total(part, slots, buf, cluster);
         if (lead) {
           const double d = apap + m2 * pp;
           const double alpha = S.rr / d;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock) batched_cg_kernel(const BatchI
           x.store(k, xv);
           accum(part, norm2(rv));
         }
-        const double rr = cluster_total((double)part, slots, buf, cluster);
+        const double rr = cluster_total(part, slots, buf, cluster);
         if (lead) {
           S.iter += 1;
           S.since_ru += 1;

@@ -117,7 +117,8 @@ struct EpiAp {
   }
   template <class A>
   __device__ __forceinline__ void finish(A* red) const {
-    double v[2] = {(double)red[0], (double)red[1]}, tot[2];
+    const A v[2] = {red[0], red[1]};
+    double tot[2];
     if (grid_sum_last_block<2>(v, partials, &sc->counter[2], tot) && threadIdx.x == 0) {
       sc->pp = tot[1];
       const double d = tot[0] + sc->m2 * tot[1];  // <p, A p> = |D_oe p|^2 + m^2 |p|^2
@@ -228,7 +229,8 @@ struct EpiUpdate {
   }
   template <class A>
   __device__ __forceinline__ void finish(A* red) const {
-    double v[1] = {(double)red[0]}, tot[1];
+    const A v[1] = {red[0]};
+    double tot[1];
     if (grid_sum_last_block<1>(v, partials, &sc->counter[3], tot) && threadIdx.x == 0) {
       const double rr = tot[0];
       sc->iter += 1;
@@ -652,10 +654,11 @@ inline int read_scalars(const CgWork& w, CgScalars* h, cudaStream_t st, int coun
 // (grid.y enumerates blocks of RB right-hand sides; partials are [rhs][kMaxPartials])
 // Write this block's RB partial sums for RHS r0..r0+RB-1; true in the block that finishes last
 // over the whole (x, y) grid.
-template <int RB>
-__device__ __forceinline__ bool mrhs_arrive(double (&v)[RB], int r0, int nrhs, double* partials, unsigned* counter) {
+template <int RB, class A>
+__device__ __forceinline__ bool mrhs_arrive(const A (&x)[RB], int r0, int nrhs, double* partials, unsigned* counter) {
   __shared__ bool am_last;
-  block_sum<RB>(v);
+  double v[RB];
+  block_sum<RB>(x, v);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < RB; ++j)

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kBlock) cg_p_mrhs_kernel(int Vh, FieldT r_all,
       accum(part, norm2(pv));
     }
   }
-  double red[1] = {(double)part};
+  const decltype(part) red[1] = {part};
   if (mrhs_arrive<1>(red, r, nrhs, partials, &sc[0].counter[kCtrK3M])) {
     __shared__ double tot[kMaxRhs];
     mrhs_totals(nrhs, partials, tot);
@@ -113,10 +113,7 @@ __global__ void __launch_bounds__(kBlock, MrhsMinBlocks<LinksT, RB>::value) dsla
         if ((active >> j) & 1u) epi.site(k, r0 + j, acc[j], part[j]);
     }
   }
-  double red[RB];
-#pragma unroll
-  for (int j = 0; j < RB; ++j) red[j] = (double)part[j];
-  if (mrhs_arrive<RB>(red, r0, nrhs, epi.partials, &epi.sc[0].counter[Epi::kCounter])) {
+  if (mrhs_arrive<RB>(part, r0, nrhs, epi.partials, &epi.sc[0].counter[Epi::kCounter])) {
     __shared__ double tot[kMaxRhs];
     mrhs_totals(nrhs, epi.partials, tot);
     // one thread per right-hand side: a serial loop over sixteen updates (dependent global loads and
@@ -210,7 +207,7 @@ __global__ void __launch_bounds__(kShThreads, ShMinBlocks<LinksT>::value) dslash
   // barrier, and thread 0 arrives for the block.
   __shared__ bool am_last;
   {
-    const double v0 = warp_sum((double)part0), v1 = warp_sum((double)part1);
+    const double v0 = warp_sum(part0), v1 = warp_sum(part1);
     if (lane == 0) {
       if (q0 < nrhs) epi.partials[(size_t)q0 * kMaxPartials + blockIdx.x] = v0;
       if (q1 < nrhs) epi.partials[(size_t)q1 * kMaxPartials + blockIdx.x] = v1;

@@ -9,6 +9,19 @@
 
 namespace qcd {
 
+// A neighbour vector v and a factor s with in(j) = s v: the FP16 field's per-site scale (its
+// load_raw), else s = 1. The unfolded-link hop multiplies U v by (sign / 2) s in one coefficient.
+template <class In>
+__device__ __forceinline__ auto load_unscaled(const In& in, int j, typename In::T& s, int)
+    -> decltype(in.load_raw(j, s)) {
+  return in.load_raw(j, s);
+}
+template <class In>
+__device__ __forceinline__ cvec3<typename In::T> load_unscaled(const In& in, int j, typename In::T& s, long) {
+  s = typename In::T(1);
+  return in.load(j);
+}
+
 // out(n) = sum_mu [ s_mu(n) U_mu(n) in(n+mu) - s_mu(n-mu) U_mu(n-mu)^dagger in(n-mu) ] / 2 for the
 // even-odd site k of parity out_par; s = eta * zeta. Folded links already carry s/2.
 template <class LinksT, class FieldT>
@@ -23,18 +36,20 @@ __device__ __forceinline__ cvec3<typename LinksT::T> hop(const Geom& g, const Li
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
     const su3<T> Uf = U.load(out_par, mu, k);
-    const cvec3<T> xf = in.load(fwd[mu]);
     if constexpr (LinksT::kFolded) {
-      mul_add(acc, Uf, xf);
+      mul_add(acc, Uf, in.load(fwd[mu]));
     } else {
-      axpy(acc, T(0.5f * fwd_sign(g, s, mu)), mul(Uf, xf));
+      T sc;
+      const cvec3<T> xf = load_unscaled(in, fwd[mu], sc, 0);
+      axpy(acc, T(0.5f * fwd_sign(g, s, mu)) * sc, mul(Uf, xf));
     }
     const su3<T> Ub = U.load(1 - out_par, mu, bwd[mu]);
-    const cvec3<T> xb = in.load(bwd[mu]);
     if constexpr (LinksT::kFolded) {
-      adj_mul_sub(acc, Ub, xb);
+      adj_mul_sub(acc, Ub, in.load(bwd[mu]));
     } else {
-      axpy(acc, T(-0.5f * bwd_sign(g, s, mu)), adj_mul(Ub, xb));
+      T sc;
+      const cvec3<T> xb = load_unscaled(in, bwd[mu], sc, 0);
+      axpy(acc, T(-0.5f * bwd_sign(g, s, mu)) * sc, adj_mul(Ub, xb));
     }
   }
   return acc;
@@ -59,7 +74,10 @@ __device__ __forceinline__ cvec3<typename LinksT::T> hop_half(const Geom& g, con
     const int li = sub ? bwd[mu] : k;
     const int xi = sub ? bwd[mu] : fwd[mu];
     const su3<T> L = U.load(lpar, mu, li);
-    const cvec3<T> xv = in.load(xi);
+    T sc = T(1);
+    cvec3<T> xv;
+    if constexpr (LinksT::kFolded) xv = in.load(xi);
+    else xv = load_unscaled(in, xi, sc, 0);
     su3<T> M;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -72,7 +90,7 @@ __device__ __forceinline__ cvec3<typename LinksT::T> hop_half(const Geom& g, con
       mul_add(acc, M, xv);
     } else {
       const float sg = sub ? bwd_sign(g, s, mu) : fwd_sign(g, s, mu);
-      axpy(acc, T(0.5f * sg), mul(M, xv));
+      axpy(acc, T(0.5f * sg) * sc, mul(M, xv));
     }
   }
   return acc;

@@ -454,6 +454,20 @@ struct Field<QCD_PREC_HALF> {
   int Vh;
   __device__ __forceinline__ cvec3<float> load(int k) const { return decode(__ldg(p + k)); }
   __device__ __forceinline__ cvec3<float> load_cg(int k) const { return decode(__ldcg(p + k)); }
+  // The colour vector without its scale, and the scale: an operator that multiplies its hop
+  // result by a coefficient anyway applies the scale there, once, instead of to six reals.
+  __device__ __forceinline__ cvec3<float> load_raw(int k, float& s) const {
+    const uint4 q = __ldg(p + k);
+    s = __uint_as_float(q.w);
+    cvec3<float> v;
+    const unsigned w[3] = {q.x, q.y, q.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 f = u32_to_float2(w[a]);
+      v.c[a].re = f.x; v.c[a].im = f.y;
+    }
+    return v;
+  }
   __device__ __forceinline__ static cvec3<float> decode(uint4 q) {
     const float s = __uint_as_float(q.w);
     cvec3<float> v;
@@ -763,6 +777,50 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   __syncthreads();
 }
 
+// The same sums for FP32 per-thread values, carried as float pairs hi + lo (Knuth's two-sum on the
+// FP32 pipes, ~48 significant bits) and returned as FP64. GB300's FP64 pipe runs at 1/64 of the FP32
+// rate: the FP64 shuffle tree (5 adds per warp and value) of every block of a one-wave launch kept
+// that pipe busy ~6k cycles per SM at the end of each FP32 or FP16 CG operator launch (ncu: FP64
+// pipe 15 % active in a kernel with no other FP64 arithmetic).
+__device__ __forceinline__ df64 warp_sum_pair(df64 t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    t = t + df64(__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o));
+  return t;
+}
+__device__ __forceinline__ double warp_sum(float v) {
+  const df64 t = warp_sum_pair(df64(v, 0.f));
+  return (double)t.hi + (double)t.lo;
+}
+template <int NV>
+__device__ __forceinline__ void block_sum(const float (&x)[NV], double (&v)[NV]) {
+  __shared__ float2 sm[NV][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  df64 t[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) t[j] = warp_sum_pair(df64(x[j], 0.f));
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sm[j][warp] = make_float2(t[j].hi, t[j].lo);
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      const float2 q = lane < nw ? sm[j][lane] : make_float2(0.f, 0.f);
+      const df64 u = warp_sum_pair(df64(q.x, q.y));
+      v[j] = (double)u.hi + (double)u.lo;
+    }
+  }
+  __syncthreads();
+}
+template <int NV>
+__device__ __forceinline__ void block_sum(const double (&x)[NV], double (&v)[NV]) {
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = x[j];
+  block_sum<NV>(v);
+}
+
 // Sum of partials[j * kMaxPartials + b] over b < n, for j < NV, by the whole block (thread 0 gets
 // the totals). The order is fixed by n and blockDim.x alone: thread t adds the blocks t + q*B in four
 // chains (q mod 4), the chains in pairs, then the block. The four chains keep a thread's loads in
@@ -797,12 +855,14 @@ __device__ __forceinline__ void sum_partials(const double* partials, int n, doub
 
 // Write this block's partials; returns true in the block that finished last, after which
 // `tot` holds the grid-wide sums (valid in every thread of that block).
-template <int NV>
-__device__ __forceinline__ bool grid_sum_last_block(double (&v)[NV], double* partials, unsigned* counter,
+// A is float (the FP32-arithmetic kernels' per-thread sums, reduced as float pairs) or double.
+template <int NV, class A>
+__device__ __forceinline__ bool grid_sum_last_block(const A (&x)[NV], double* partials, unsigned* counter,
                                                     double (&tot)[NV]) {
   __shared__ bool am_last;
   __shared__ double res[NV];
-  block_sum<NV>(v);
+  double v[NV];
+  block_sum<NV>(x, v);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) partials[(size_t)j * kMaxPartials + blockIdx.x] = v[j];

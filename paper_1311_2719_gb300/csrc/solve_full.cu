@@ -40,7 +40,8 @@ struct EpiSource {
   }
   template <class A>
   __device__ __forceinline__ void finish(A* red) const {
-    double v[2] = {(double)red[0], (double)red[1]}, tot[2];
+    const A v[2] = {red[0], red[1]};
+    double tot[2];
     if (grid_sum_last_block<2>(v, partials, counter, tot) && threadIdx.x == 0) {
       sums[0] = tot[0];
       sums[1] = tot[1];
@@ -74,7 +75,8 @@ struct EpiFullResidual {
   }
   template <class A>
   __device__ __forceinline__ void finish(A* red) const {
-    double v[2] = {(double)red[0], (double)red[1]}, tot[2];
+    const A v[2] = {red[0], red[1]};
+    double tot[2];
     if (grid_sum_last_block<2>(v, partials, counter, tot) && threadIdx.x == 0) {
       out[0] += tot[0];
       out[1] += tot[1];

@@ -417,8 +417,9 @@ __global__ void __launch_bounds__(kBlock, WMrhsMinBlocks<typename LinksT::T, RB>
   if constexpr (Epi::kReduce) {
     __shared__ bool am_last;
     for (int q = 0; q < nrhs; ++q) {
-      double v[1] = {(double)spart[q][threadIdx.x]};
-      block_sum<1>(v);
+      const A x[1] = {spart[q][threadIdx.x]};
+      double v[1];
+      block_sum<1>(x, v);
       if (threadIdx.x == 0) epi.partials[(size_t)q * kMaxPartials + blockIdx.x] = v[0];
     }
     if (threadIdx.x == 0) {
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(kShThreads, WShMinBlocks<typename LinksT::T>::
     // the block's partial for RHS q is warp (q mod kShWarps)'s sum; its writer fences before the
     // barrier, thread 0 arrives for the block
     __shared__ bool am_last;
-    const double v0 = warp_sum((double)part[0]), v1 = warp_sum((double)part[1]);
+    const double v0 = warp_sum(part[0]), v1 = warp_sum(part[1]);
     if (lane == 0) {
       if (w < nrhs) epi.partials[(size_t)w * kMaxPartials + blockIdx.x] = v0;
       if (w + kShWarps < nrhs) epi.partials[(size_t)(w + kShWarps) * kMaxPartials + blockIdx.x] = v1;
@@ -686,7 +687,8 @@ struct WEpiResidual {
   }
   template <class A>
   __device__ __forceinline__ void finish(A* red) const {
-    double v[1] = {(double)red[0]}, tot[1];
+    const A v[1] = {red[0]};
+    double tot[1];
     if (grid_sum_last_block<1>(v, partials, &sc->counter[4], tot) && threadIdx.x == 0) {
       const double rr = tot[0];
       sc->res2 = rr;
@@ -751,7 +753,8 @@ struct WEpiReliableInner {
   }
   template <class A>
   __device__ __forceinline__ void finish(A* red) const {
-    double v[1] = {(double)red[0]}, tot[1];
+    const A v[1] = {red[0]};
+    double tot[1];
     if (grid_sum_last_block<1>(v, partials, &sc->counter[4], tot) && threadIdx.x == 0) {
       const double rr = tot[0];
       if (!isfinite(rr)) { sc->done = kBreakdown; return; }

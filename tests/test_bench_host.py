@@ -61,7 +61,7 @@ def test_source_hash_covers_names_and_contents(tmp_path, monkeypatch):
 def test_default_workload_is_the_32_4_mixed_solve():
     wl = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
     assert wl["kind_solve"] == "mixed32" and wl["dims"] == (32, 32, 32, 32)
-    assert wl["inner"] == "single12" and wl["mass"] == 0.01 and wl["tol"] == 1e-10
+    assert wl["inner"] == "half12" and wl["mass"] == 0.01 and wl["tol"] == 1e-10
 
 
 def test_k1_k2_bytes_match_the_per_site_table():
