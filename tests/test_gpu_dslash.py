@@ -4,6 +4,7 @@ import pytest
 
 from oracle import staggered as S
 from paper_1311_2719_gb300 import inputs as I
+from paper_1311_2719_gb300 import qcd as Q
 
 pytestmark = pytest.mark.gpu
 
@@ -157,3 +158,76 @@ def test_full_size_24_4_sixteen_rhs_sampled(H):
     sites = _sample_sites(dims, 0, 1000, seed=7)
     for r in range(16):
         assert H.rel(got[r][sites], S.dslash_sites(U, xs[r], dims, sites)) <= 1e-5, r
+
+
+# ---- the 16-bit formats, written out from their definitions (test-side; the oracle is FP64)
+def _fx16(v):
+    """16-bit fixed-point code of reals |v| <= 1: round(fl32(v) * 2^15) + 2^15, saturated to 16 bits."""
+    t = np.rint(np.asarray(v).astype(np.float32) * np.float32(32768.0))
+    return (np.clip(t, -32768.0, 32767.0).astype(np.int64) + 32768).astype(np.uint32)
+
+
+def _eo_lex(dims, par):
+    """Canonical index of even-odd site k (k = 0 .. V/2-1) of parity `par`: the canonical pair
+    (2k, 2k+1) shares x1..x3 and holds one site of each parity."""
+    L0, L1, L2, _ = dims
+    j = 2 * np.arange(int(np.prod(dims)) // 2)
+    x0e, t = j % L0, j // L0
+    x1, t1 = t % L1, t // L1
+    x2, x3 = t1 % L2, t1 // L2
+    return j + ((x1 + x2 + x3 + par) & 1)
+
+
+def _half_field(x):
+    """A canonical field quantised as the 16-bit vector format stores it: per site m = max |re|, |im|
+    over the colours (FP32), each component fl16(fl32(v) * fl32(1 / m)), read back as that times m."""
+    re, im = x.real.astype(np.float32), x.imag.astype(np.float32)
+    m = np.maximum(np.abs(re).max(axis=1), np.abs(im).max(axis=1))
+    inv = np.where(m > 0, np.float32(1.0) / np.where(m > 0, m, np.float32(1.0)), np.float32(0.0)).astype(np.float32)
+    qr = (re * inv[:, None]).astype(np.float16).astype(np.float64)
+    qi = (im * inv[:, None]).astype(np.float16).astype(np.float64)
+    return (qr + 1j * qi) * m.astype(np.float64)[:, None], m.astype(np.float64)
+
+
+def test_fixed_point_links_are_bit_exact(H):
+    """QCD_PREC_HALF recon-12 links are integer data: each 32-bit word is the (re, im) pair of one
+    element of rows 0 and 1 in 16-bit fixed point, laid out [parity][mu][site] as four words
+    (elements 00 01 02 10) and then, after all of them, two words (11 12)."""
+    dims = (4, 6, 2, 8)
+    U = I.make_links(dims, kind="haar", seed=3)
+    U[5, 2] = np.eye(3)    # elements 1 and 0: the saturated code and the bias
+    U[7, 1] = -np.eye(3)   # -1: the lowest code
+    rig = H.Rig(dims, U, precs=[])
+    words = H.host(rig.lat.load_links(rig.U_dev, Q.QCD_PREC_HALF, 12)).view(np.uint32)
+    Vh = U.shape[0] // 2
+    assert words.size == 8 * Vh * 6
+    A = words[: 8 * Vh * 4].reshape(2, 4, Vh, 4)
+    B = words[8 * Vh * 4:].reshape(2, 4, Vh, 2)
+    for par in (0, 1):
+        E = U[_eo_lex(dims, par)][:, :, :2, :].reshape(Vh, 4, 6)
+        W = (_fx16(E.real) | (_fx16(E.imag) << np.uint32(16))).transpose(1, 0, 2)
+        assert np.array_equal(A[par], W[..., :4]) and np.array_equal(B[par], W[..., 4:]), par
+
+
+@pytest.mark.parametrize("dims,out_par", [((4, 6, 2, 8), 1), ((6, 4, 4, 4), 0)])
+def test_16bit_operator_matches_oracle_on_its_quantised_inputs(H, dims, out_par):
+    """The 16-bit operator, fed links and a vector that are exact in its formats, differs from the
+    FP64 oracle on the same quantised inputs by FP32 arithmetic and the output's FP16 rounding only:
+    per site at most 2^-11 of the site's largest component (half an FP16 step is 2^-12)."""
+    U = I.make_links(dims, kind="haar", seed=5)
+    x = I.make_source(dims, seed=6)
+    Uq = U.copy()
+    rows = _fx16(np.stack([U[:, :, :2, :].real, U[:, :, :2, :].imag], -1)).astype(np.float64)
+    deq = (rows - 32768.0) / 32768.0
+    Uq[:, :, :2, :] = deq[..., 0] + 1j * deq[..., 1]
+    a, b = Uq[:, :, 0, :], Uq[:, :, 1, :]
+    Uq[:, :, 2, :] = np.conj(np.cross(a, b))  # the third row as every recon-12 kernel rebuilds it
+    rig = H.Rig(dims, U, precs=["half12"])
+    xin = np.where((S.parity(dims) != out_par)[:, None], _half_field(x)[0], 0.0)
+    want = S.dslash_parity(Uq, xin, dims, out_par)
+    got = rig.dslash(xin, out_par, "half12")
+    sites = S.parity(dims) == out_par
+    m = np.max(np.abs(np.stack([want.real, want.imag], -1)), axis=(1, 2))
+    err = np.max(np.abs(np.stack([(got - want).real, (got - want).imag], -1)), axis=(1, 2))
+    assert np.all(err[sites] <= 2.0 ** -11 * m[sites]), float(np.max(err[sites] / m[sites]))
+    assert np.all(got[~sites] == 0)
