@@ -114,6 +114,8 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "cg32_mixed"
 PRECS = {"double": (0, 18), "single18": (1, 18), "single12": (1, 12), "half12": (2, 12), "df64": (3, 18)}
+# the default line's config-4 legs (multi-RHS and many-lattice solves), at the headline's precision
+BATCHED_LEGS = ("mrhs24_half12", "batch64_half12")
 NAMES = {"double": "FP64", "single18": "FP32 recon-18", "single12": "FP32 recon-12",
          "half12": "16-bit recon-12 (fixed-point links, FP16 vectors)", "df64": "df64"}
 DTYPE = {"double": "f64", "single18": "f32 (FP64 reliable updates)", "single12": "f32 (FP64 reliable updates)",
@@ -688,7 +690,7 @@ def run_gpu_mixed32(args, wl):
     # ---- config 4: the multi-RHS and many-lattice solves (their own lattices and sources)
     batched = {}
     if not args.no_batched and not args.no_legs:
-        for key in ("mrhs24_half12", "batch64_half12"):
+        for key in BATCHED_LEGS:
             # launch shapes chosen by the library's autotuner first (outside the timed steps)
             bl = batched_leg(WORKLOADS[key], leg_steps if key.startswith("mrhs") else max(leg_steps, 5), 1, True,
                              key, world, local, fp64_steps=max(1, min(leg_steps, 2)), sample_clocks=False)

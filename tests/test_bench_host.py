@@ -64,6 +64,17 @@ def test_default_workload_is_the_32_4_mixed_solve():
     assert wl["inner"] == "half12" and wl["mass"] == 0.01 and wl["tol"] == 1e-10
 
 
+def test_default_line_batched_legs_run_at_the_headline_precision():
+    head = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]["inner"]
+    kinds = set()
+    for key in bench.BATCHED_LEGS:
+        wl = bench.WORKLOADS[key]
+        kinds.add(wl["kind_solve"])
+        assert wl["inner"] == head and wl["tol"] == 1e-10
+    assert kinds == {"mrhs", "batched"}
+    assert bench.WORKLOADS["mrhs24_half12"]["nrhs"] == 16 and bench.WORKLOADS["batch64_half12"]["n"] == 64
+
+
 def test_k1_k2_bytes_match_the_per_site_table():
     # FP64 K1 = 1152 + 2*48, K2 = 1152 + 48 + 2*48 + 48 + 48 + 48; FP32 recon-12 and FP16 recon-12
     assert bench._k1_k2_bytes("double") == (1248, 1440)
