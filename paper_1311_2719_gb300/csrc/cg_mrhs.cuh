@@ -420,12 +420,16 @@ int mrhs_typed(qcd_lattice* lat, int R, void* x, const void* b, double mass, dou
   M.st = st;
   M.grid = cg_grid<PREC, RECON>(lat->Vh, 1);
   M.R = R;
-  M.rb = o.rhs_block;
-  if ((PREC == QCD_PREC_DOUBLE || PREC == QCD_PREC_DF64) && M.rb > 4) M.rb = 4;
-  if (M.rb <= 0) {
+  constexpr bool wide = PREC == QCD_PREC_DOUBLE || PREC == QCD_PREC_DF64;  // 64-bit accumulators: RB <= 4
+  M.rb = o.rhs_block;  // -1: the shared-link kernel; 0: tuned or default
+  if (wide && M.rb > 4) M.rb = 4;
+  if (M.rb == 0) {
+    // a tuned value read from a cache file is used only if this precision supports it
     std::vector<int> tuned;
-    M.rb = tune_lookup(mrhs_key(lat, PREC, RECON, R), &tuned) ? tuned[0]
-                                                                : default_rhs_block(PREC, R, links_bytes(PREC, RECON, lat->Vh));
+    const bool have = tune_lookup(mrhs_key(lat, PREC, RECON, R), &tuned) && !tuned.empty() &&
+                      (tuned[0] == kRhsShared || tuned[0] == 1 || tuned[0] == 2 || tuned[0] == 4 ||
+                       (!wide && (tuned[0] == 8 || tuned[0] == 16)));
+    M.rb = have ? tuned[0] : default_rhs_block(PREC, R, links_bytes(PREC, RECON, lat->Vh));
   }
   const bool mixed = PREC != QCD_PREC_DOUBLE;
   const size_t canon_bytes = (size_t)lat->V * 3 * sizeof(double2);
