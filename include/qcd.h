@@ -372,7 +372,8 @@ QCD_API int qcd_tune_batched(int n, qcd_lattice* const lats[], void* const x[], 
                      const double mass[], double tol, int max_iter, const qcd_solver_opts* opts,
                      void* workspace_dev, const char* cache_path, int* best_cluster, int* best_block,
                      void* stream);
-/* Load tuned entries written by the two calls above (missing file = nothing to load). */
+/* Load tuned entries written by the two calls above (missing file = nothing to load; a line whose
+ * shape the solvers do not accept, e.g. hand-edited or truncated, is skipped). */
 QCD_API int qcd_tune_load(const char* cache_path);
 
 #ifdef __cplusplus

@@ -1,7 +1,8 @@
 // Autotuner for the launch shapes of the batched solvers.
 //
 // qcd_tune_mrhs times the multi-RHS solver's operator launches (CUDA events, a short run of the
-// real solve) for every register block of right-hand sides; qcd_tune_batched times the whole
+// real solve) for the shared-link kernel and every register block of right-hand sides;
+// qcd_tune_batched times the whole
 // persistent batched solve for every (cluster size, block size) pair. The winner is kept in an
 // in-process table that the solvers consult when the corresponding option is 0, and appended to
 // an optional text cache (one "key value..." line per entry) that qcd_tune_load reads back.
@@ -81,6 +82,18 @@ using namespace qcd;
 
 extern "C" {
 
+// A cached entry is loaded only if its values are launch shapes the solvers accept: a multi-RHS
+// block of -1 (shared-link kernel), 1, 2, 4, 8 or 16; a cluster of 1-16 blocks (a power of two) of
+// 32-256 threads (a multiple of 32). A hand-edited or truncated line is skipped, not launched.
+static bool valid_entry(const std::string& key, const std::vector<int>& v) {
+  if (key.compare(0, 5, "mrhs|") == 0)
+    return v[0] == -1 || v[0] == 1 || v[0] == 2 || v[0] == 4 || v[0] == 8 || v[0] == 16;
+  if (key.compare(0, 8, "batched|") == 0)
+    return v.size() >= 2 && v[0] >= 1 && v[0] <= 16 && (v[0] & (v[0] - 1)) == 0 && v[1] >= 32 && v[1] <= 256 &&
+           v[1] % 32 == 0;
+  return false;
+}
+
 int qcd_tune_load(const char* cache_path) {
   if (!cache_path) {
     set_error("cache_path is NULL");
@@ -97,7 +110,7 @@ int qcd_tune_load(const char* cache_path) {
     std::string key = tok;
     std::vector<int> v;
     while ((tok = strtok_r(nullptr, " \n", &save))) v.push_back(atoi(tok));
-    if (!v.empty()) g_tune[key] = v;  // later lines win
+    if (!v.empty() && valid_entry(key, v)) g_tune[key] = v;  // later lines win
   }
   fclose(f);
   return QCD_OK;

@@ -130,3 +130,21 @@ def test_wilson_byte_counts():
         assert Q.qcd_wilson_workspace_bytes(h, o, 2) == 0
     finally:
         Q.qcd_lattice_destroy(h)
+
+
+def test_tune_cache_loader_skips_shapes_the_solvers_reject(tmp_path):
+    """qcd_tune_load parses its text cache on the host: a missing file is not an error, malformed
+    or unsupported lines are skipped, a NULL path is rejected."""
+    from paper_1311_2719_gb300 import qcd as Q
+    Q.qcd_tune_load(str(tmp_path / "absent.txt"))
+    p = tmp_path / "tune.txt"
+    p.write_text("mrhs|X|4x4x4x4|p1|r12|n8 3 100\n"        # RHS block 3: not a shape
+                 "mrhs|X|4x4x4x4|p1|r12|n8 -1 100\n"       # the shared-link kernel
+                 "batched|X|n4|v1024|p1|r12 0 128 5\n"      # cluster 0
+                 "batched|X|n4|v1024|p1|r12 4 100 5\n"      # block not a multiple of 32
+                 "garbage\n\n"
+                 "batched|X|n4|v1024|p1|r12 4 128\n")
+    Q.qcd_tune_load(str(p))
+    with pytest.raises(Q.QcdError) as e:
+        Q._check(Q._lib.qcd_tune_load(None), "qcd_tune_load")
+    assert e.value.status == Q.QCD_ERR_INVALID_ARG
