@@ -390,6 +390,10 @@ int check_batched_args(int n, qcd_lattice* const lats[], void* const x[], const 
   if (opts) o = *opts;
   if (!valid_prec(o.prec_inner)) return invalid("unknown inner precision %d", o.prec_inner);
   if (o.reliable_delta < 0.0 || o.reliable_delta >= 1.0) return invalid("reliable_delta must be in [0, 1)");
+  if (o.cluster_size != 0 && (o.cluster_size < 1 || o.cluster_size > 16 || (o.cluster_size & (o.cluster_size - 1))))
+    return invalid("cluster_size must be 0 (tuned) or a power of two <= 16, got %d", o.cluster_size);
+  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32 != 0))
+    return invalid("block_size must be 0 (tuned) or a multiple of 32 in [32, 256], got %d", o.block_size);
   int dev = -1;
   cudaGetDevice(&dev);
   int recon0 = 0;

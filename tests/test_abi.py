@@ -93,6 +93,16 @@ def test_calls_reject_bad_arguments_before_device_work():
             assert rc == Q.QCD_ERR_INVALID_ARG and info["status"] == rc
         rc, _ = Q.qcd_cg_solve(h, fake, fake + 256, 0.1, 1e-10, 10, o, fake + 512, raise_on=())
         assert rc == Q.QCD_ERR_NO_LINKS
+        # batched launch shapes: 0 (tuned) or a supported cluster / block size
+        for cs, bs in [(3, 0), (-4, 0), (32, 0), (0, 100), (0, 16), (0, 512), (0, -32)]:
+            ob = Q.qcd_solver_opts_default()
+            ob.cluster_size, ob.block_size = cs, bs
+            rc, _ = Q.qcd_cg_solve_batched([h], [fake], [fake + 256], None, [0.1], 1e-10, 10, ob, fake + 512,
+                                           raise_on=())
+            assert rc == Q.QCD_ERR_INVALID_ARG, (cs, bs)
+        rc, _ = Q.qcd_cg_solve_batched([h], [fake], [fake + 256], None, [0.1], 1e-10, 10,
+                                       Q.qcd_solver_opts_default(), fake + 512, raise_on=())
+        assert rc == Q.QCD_ERR_NO_LINKS
     finally:
         Q.qcd_lattice_destroy(h)
 
